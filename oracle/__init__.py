@@ -1,0 +1,242 @@
+"""Plain FP64 CPU oracle of the kinetic DG step (TEST INFRASTRUCTURE ONLY).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never loads it and
+shares no code with it; the C source (``kin_oracle.c``) follows the paper's
+Sec. 2.2 (kinetic algorithm), Sec. 3 (implicit upwind DG, eq. dg_imp, with
+Crank-Nicolson in time, downwind solve) and Sec. 5.1 (subdomain iteration,
+eq. ibvp), in FP64.
+
+Arrays use the storage order of ``kin_oracle.h``:
+``W[v][cz][cy][cx][nz][ny][nx]`` and ``f[pop][...]`` with ``pop = k*m + v``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kin_oracle.c")
+_HDR = os.path.join(_HERE, "kin_oracle.h")
+_LIB = os.path.join(_HERE, "libkin_oracle.so")
+
+ADVECTION = 0
+EULER = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, portable: x86_64 and aarch64).
+
+    ``KIN_ORACLE_LIB`` names a prebuilt oracle library to load instead (used
+    by the planted-mistake test, which builds altered copies of the source)."""
+    override = os.environ.get("KIN_ORACLE_LIB")
+    if override:
+        return override
+    stale = (not os.path.exists(_LIB)) or any(
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+    if force or stale:
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("degree", ctypes.c_int),
+        ("system", ctypes.c_int),
+        ("lam", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("adv", ctypes.c_double * 3),
+        ("omega", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("tiles", ctypes.c_int * 3),
+        ("iters", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        pp = ctypes.POINTER(_Problem)
+        ip = ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "ko_num_vars": ([pp], ctypes.c_int),
+            "ko_num_vel": ([pp], ctypes.c_int),
+            "ko_num_nodes": ([pp], ctypes.c_size_t),
+            "ko_gll": ([ctypes.c_int, dp, dp], ctypes.c_int),
+            "ko_diff_matrix": ([ctypes.c_int, dp], ctypes.c_int),
+            "ko_node_coords": ([pp, dp], ctypes.c_int),
+            "ko_flux": ([pp, dp, ctypes.c_int, dp], ctypes.c_int),
+            "ko_maxwellian": ([pp, dp, dp], ctypes.c_int),
+            "ko_cell_matrix": ([pp, ctypes.c_int, dp], ctypes.c_int),
+            "ko_init": ([pp, dp, dp], ctypes.c_int),
+            "ko_moments": ([pp, dp, dp], ctypes.c_int),
+            "ko_transport": ([pp, dp, dp, ip], ctypes.c_int),
+            "ko_relax": ([pp, dp], ctypes.c_int),
+            "ko_step": ([pp, dp, ctypes.c_int], ctypes.c_int),
+            "ko_mass": ([pp, dp, dp], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(_lib, name)
+            fn.argtypes = args
+            fn.restype = res
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+@dataclass
+class Problem:
+    """A periodic Cartesian kinetic DG problem (mirrors ``ko_problem``)."""
+    dim: int
+    n: tuple
+    lo: tuple
+    hi: tuple
+    degree: int
+    system: int
+    lam: float
+    dt: float
+    omega: float = 2.0
+    gamma: float = 1.4
+    adv: tuple = (1.0, 0.0, 0.0)
+    tiles: tuple = (1, 1, 1)
+    iters: int = 3
+    _c: _Problem = field(default=None, repr=False, compare=False)
+
+    def c(self) -> _Problem:
+        def pad(t, fill):
+            t = tuple(t)
+            return t + (fill,) * (3 - len(t))
+        p = _Problem()
+        p.dim = self.dim
+        p.n = (ctypes.c_int * 3)(*pad(self.n, 1))
+        p.lo = (ctypes.c_double * 3)(*pad(self.lo, 0.0))
+        p.hi = (ctypes.c_double * 3)(*pad(self.hi, 1.0))
+        p.degree = self.degree
+        p.system = self.system
+        p.lam = self.lam
+        p.gamma = self.gamma
+        p.adv = (ctypes.c_double * 3)(*pad(self.adv, 0.0))
+        p.omega = self.omega
+        p.dt = self.dt
+        p.tiles = (ctypes.c_int * 3)(*pad(self.tiles, 1))
+        p.iters = self.iters
+        self._c = p
+        return p
+
+    @property
+    def m(self) -> int:
+        return lib().ko_num_vars(ctypes.byref(self.c()))
+
+    @property
+    def nvel(self) -> int:
+        return 2 * self.dim
+
+    @property
+    def npop(self) -> int:
+        return self.nvel * self.m
+
+    @property
+    def nodes(self) -> int:
+        return int(lib().ko_num_nodes(ctypes.byref(self.c())))
+
+
+def gll(p: int):
+    xi = np.zeros(p + 1)
+    w = np.zeros(p + 1)
+    _check(lib().ko_gll(p, _dp(xi), _dp(w)), "gll")
+    return xi, w
+
+
+def diff_matrix(p: int) -> np.ndarray:
+    D = np.zeros((p + 1) * (p + 1))
+    _check(lib().ko_diff_matrix(p, _dp(D)), "diff_matrix")
+    return D.reshape(p + 1, p + 1)
+
+
+def node_coords(P: Problem) -> np.ndarray:
+    xyz = np.zeros(3 * P.nodes)
+    _check(lib().ko_node_coords(ctypes.byref(P.c()), _dp(xyz)), "node_coords")
+    return xyz.reshape(-1, 3)
+
+
+def flux(P: Problem, W, axis: int) -> np.ndarray:
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    Q = np.zeros(P.m)
+    _check(lib().ko_flux(ctypes.byref(P.c()), _dp(W), axis, _dp(Q)), "flux")
+    return Q
+
+
+def maxwellian(P: Problem, W) -> np.ndarray:
+    """M_k(W) at one point, shape (nvel, m)."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    M = np.zeros(P.npop)
+    _check(lib().ko_maxwellian(ctypes.byref(P.c()), _dp(W), _dp(M)), "maxwellian")
+    return M.reshape(P.nvel, P.m)
+
+
+def cell_matrix(P: Problem, k: int) -> np.ndarray:
+    nn = (P.degree + 1) ** P.dim
+    A = np.zeros(nn * nn)
+    _check(lib().ko_cell_matrix(ctypes.byref(P.c()), k, _dp(A)), "cell_matrix")
+    return A.reshape(nn, nn)
+
+
+def init(P: Problem, W0: np.ndarray) -> np.ndarray:
+    W0 = np.ascontiguousarray(W0, dtype=np.float64).reshape(-1)
+    assert W0.size == P.m * P.nodes
+    f = np.zeros(P.npop * P.nodes)
+    _check(lib().ko_init(ctypes.byref(P.c()), _dp(W0), _dp(f)), "init")
+    return f
+
+
+def moments(P: Problem, f: np.ndarray) -> np.ndarray:
+    W = np.zeros(P.m * P.nodes)
+    _check(lib().ko_moments(ctypes.byref(P.c()), _dp(f), _dp(W)), "moments")
+    return W
+
+
+def transport(P: Problem, f: np.ndarray):
+    """In-place CN transport; returns (per-variable interface mass defect, iterations)."""
+    defect = np.zeros(P.m)
+    it = ctypes.c_int(0)
+    _check(lib().ko_transport(ctypes.byref(P.c()), _dp(f), _dp(defect), ctypes.byref(it)),
+           "transport")
+    return defect, it.value
+
+
+def relax(P: Problem, f: np.ndarray) -> None:
+    _check(lib().ko_relax(ctypes.byref(P.c()), _dp(f)), "relax")
+
+
+def step(P: Problem, f: np.ndarray, nsteps: int = 1) -> None:
+    _check(lib().ko_step(ctypes.byref(P.c()), _dp(f), nsteps), "step")
+
+
+def mass(P: Problem, W: np.ndarray) -> np.ndarray:
+    out = np.zeros(P.m)
+    _check(lib().ko_mass(ctypes.byref(P.c()), _dp(np.ascontiguousarray(W)), _dp(out)), "mass")
+    return out

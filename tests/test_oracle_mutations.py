@@ -1,0 +1,62 @@
+"""The oracle's pins must catch plausible mistakes: each case below plants
+one (a flipped sign, a dropped term, a transposed operand, a wrong index or
+iterate) in a copy of the oracle source, builds it into a scratch library and
+requires the pin suite to fail against it."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+from tests.conftest import ROOT
+
+SRC = os.path.join(ROOT, "oracle", "kin_oracle.c")
+
+MUTATIONS = {
+    "volume_term_sign": ("A[i * nn + q] -= tau * vol_weight(P, w, q) * vg;",
+                         "A[i * nn + q] += tau * vol_weight(P, w, q) * vg;"),
+    "outflow_face_dropped": ("if (vn > 0 && on_face) A[i * nn + i] += tau * vn * face_weight(P, w, i, a);",
+                             "if (0) {}"),
+    "diff_matrix_transposed": ("vg += V[a] * D[iq[a] * np + ii[a]] / cell_size(P, a);",
+                               "vg += V[a] * D[ii[a] * np + iq[a]] / cell_size(P, a);"),
+    "interface_uses_current_iterate": ("const double* src = boundary ? prev : cur;",
+                                       "const double* src = cur;"),
+    "interior_uses_previous_iterate": ("const double* src = boundary ? prev : cur;",
+                                       "const double* src = prev;"),
+    "crank_nicolson_extrapolation_dropped": ("f[i] = 2.0 * cur[i] - f[i];", "f[i] = cur[i];"),
+    "maxwellian_flux_sign": ("M[(2 * a) * m + v] = W[v] / (2.0 * d) + Q[v] / (2.0 * P->lambda);",
+                             "M[(2 * a) * m + v] = W[v] / (2.0 * d) - Q[v] / (2.0 * P->lambda);"),
+    "pressure_dropped": ("Q[1 + b] = W[1 + b] * ua + (b == axis ? pr : 0.0);",
+                         "Q[1 + b] = W[1 + b] * ua;"),
+    "relaxation_sign": ("*fp = P->omega * M[pop] + (1.0 - P->omega) * (*fp);",
+                        "*fp = P->omega * M[pop] - (1.0 - P->omega) * (*fp);"),
+    "inflow_node_index": ("b[i] += tau * (-vn) * C->facew[a][i] * src[nbase + C->acr[a][i]];",
+                          "b[i] += tau * (-vn) * C->facew[a][i] * src[nbase + i];"),
+    "half_step_is_full_step": ("double tau = 0.5 * P->dt;\n    size_t base",
+                               "double tau = P->dt;\n    size_t base"),
+    "kinetic_energy_factor": ("ke *= 0.5 / rho;", "ke *= 1.0 / rho;"),
+    "gll_weight_power": ("w[j] = 0.5 * 2.0 / (p * (p + 1.0) * pp * pp);",
+                         "w[j] = 0.5 * 2.0 / (p * (p + 1.0) * pp);"),
+    "sweep_direction": ("if (C->V[a] < 0) {", "if (C->V[a] > 0) {"),
+}
+
+PIN_FILES = ["tests/test_oracle_basis.py", "tests/test_oracle_relaxation.py",
+             "tests/test_oracle_transport.py"]
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    before, after = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(before) >= 1, "mutation anchor vanished from the oracle source"
+    mutated = tmp_path / "kin_oracle.c"
+    mutated.write_text(src.replace(before, after, 1))
+    hdr = os.path.join(ROOT, "oracle", "kin_oracle.h")
+    (tmp_path / "kin_oracle.h").write_text(open(hdr).read())
+    lib = tmp_path / "libkin_oracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", str(mutated),
+                           "-o", str(lib), "-lm"])
+    env = dict(os.environ, KIN_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"]
+                       + PIN_FILES, cwd=ROOT, env=env, capture_output=True, text=True)
+    assert r.returncode == 1, f"planted mistake '{name}' passed every pin:\n{r.stdout[-800:]}"

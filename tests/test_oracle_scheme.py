@@ -1,0 +1,100 @@
+"""Whole-scheme pins for the oracle: exact solutions of the conservation law,
+the time order of the kinetic algorithm (second order for omega = 2, first for
+omega = 1; Sec. 2.2 remark and Sec. 2.4), subdomain consistency (Sec. 6.2: the
+subdomain results match the single-domain ones) and conservation."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+
+def _run(w, T=None, nsteps=None):
+    P = oracle.Problem(**w.oracle_kwargs())
+    f = oracle.init(P, w.W0)
+    if nsteps is None:
+        nsteps = int(round(T / w.dt))
+    oracle.step(P, f, nsteps)
+    W = oracle.moments(P, f).reshape(w.m, -1)
+    return W, nsteps * w.dt
+
+
+def _orders(errs):
+    e = np.asarray(errs)
+    return np.log2(e[:-1] / e[1:])
+
+
+def test_time_order_two_for_omega_2():
+    errs = []
+    for dt in (0.04, 0.02, 0.01):
+        w = workloads.advection1d(seed=0, n=64, dt=dt, omega=2.0, degree=3)
+        W, t = _run(w, T=0.8)
+        errs.append(np.abs(W - w.exact(t)).max())
+    assert np.all(np.abs(_orders(errs) - 2.0) < 0.1), errs
+
+
+def test_time_order_one_for_omega_1():
+    errs = []
+    for dt in (0.004, 0.002, 0.001):
+        w = workloads.advection1d(seed=0, n=64, dt=dt, omega=1.0, degree=3)
+        W, t = _run(w, T=0.2)
+        errs.append(np.abs(W - w.exact(t)).max())
+    assert np.all(np.abs(_orders(errs) - 1.0) < 0.1), errs
+
+
+def test_euler_density_wave_2d_time_order():
+    base = workloads.densitywave2d(seed=3, n=16, degree=3, tiles=2)
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        w = workloads.with_(base, dt=dt)
+        W, t = _run(w, T=0.2)
+        errs.append(np.abs(W - w.exact(t)).max())
+    assert np.all(np.abs(_orders(errs) - 2.0) < 0.15), errs
+
+
+def test_euler_density_wave_3d_converges():
+    # p = 1 on 4^3 .. 16^3 cells is still pre-asymptotic for a wave along the
+    # diagonal; the error must nevertheless fall steadily under refinement.
+    errs = []
+    for n in (4, 8, 16):
+        w = workloads.densitywave3d(seed=2, n=n, degree=1, tiles=2)
+        W, t = _run(w, T=0.1)
+        errs.append(np.abs(W - w.exact(t)).max())
+    assert errs[1] < errs[0] / 2.0 and errs[2] < errs[1] / 1.5, errs
+
+
+def test_isentropic_vortex_converges():
+    errs = []
+    for n in (16, 32, 64):
+        w = workloads.vortex2d(seed=0, n=n, degree=2, tiles=2)
+        W, t = _run(w, T=0.5)
+        errs.append(np.abs(W - w.exact(t)).max())
+    assert np.all(_orders(errs) > 1.4), errs
+
+
+def test_advection_1d_config_one_vs_four_subdomains():
+    # 256 cells, p = 1, lambda = 2, dt = 4h/lambda, 100 steps: the interface
+    # coupling decays like (8/13)^64 per subdomain, far below round-off.
+    w1 = workloads.advection1d(seed=1, n=256, tiles=1)
+    w4 = workloads.advection1d(seed=1, n=256, tiles=4)
+    W1, t = _run(w1, nsteps=w1.steps)
+    W4, _ = _run(w4, nsteps=w4.steps)
+    np.testing.assert_allclose(W4, W1, rtol=1e-12, atol=1e-12)
+    assert np.abs(W1 - w1.exact(t)).max() < 0.03
+
+
+@pytest.mark.parametrize("tiles,iters", [((2, 2), 1), ((2, 2), 3), ((4, 1), 2)])
+def test_euler_mass_change_equals_interface_defect(tiles, iters):
+    # a localised vortex: a plane wave would make the defects cancel along
+    # every line of interface faces
+    w = workloads.vortex2d(seed=4, n=8, degree=2, tiles=1, dt_mult=40.0)
+    w = workloads.with_(w, tiles=tiles, iters=iters)
+    P = oracle.Problem(**w.oracle_kwargs())
+    f = oracle.init(P, w.W0)
+    for _ in range(3):
+        m0 = oracle.mass(P, oracle.moments(P, f))
+        defect, _ = oracle.transport(P, f)
+        oracle.relax(P, f)
+        m1 = oracle.mass(P, oracle.moments(P, f))
+        np.testing.assert_allclose(m1 - m0, defect, atol=1e-13)
+        assert np.abs(defect).max() > 1e-8

@@ -1,0 +1,250 @@
+"""Seeded synthetic workloads shared by the oracle side and the CUDA side.
+
+This module holds the problem recipes only: domain, mesh, kinetic speed,
+time step, subdomain tiling and the initial data sampled at the cell nodes.
+It contains none of the scheme's arithmetic (no transport, no Maxwellian, no
+relaxation) and imports neither the oracle nor the CUDA library.
+
+Storage order of a macroscopic field ``W``: ``[v][cz][cy][cx][nz][ny][nx]``
+(cells row-major with x fastest, then the tensor Gauss-Lobatto nodes of the
+cell with the x node fastest).  The node positions inside a cell are the
+Gauss-Lobatto points of degree p on [0, 1], written here from their closed
+forms (p <= 3) so that this module depends on nothing else.
+
+Workloads (the paper's experiments use Maxwell on tetrahedral meshes that are
+not available; these periodic Cartesian problems stand in for them):
+
+* ``advection1d``  scalar u_t + a u_x = 0 on [0,1], D1Q2, p = 1, 256 cells,
+  lambda = 2, dt = 4h/lambda, omega = 2, u0 = A sin(2 pi x) + B with
+  A, B ~ U(0.5, 1.5) from the seed; FP64.
+* ``vortex2d``     Euler (gamma = 1.4) on [0,10]^2, D2Q4, p = 2, 256^2 cells,
+  isentropic vortex (centre ~ U(box), strength ~ U(3, 5), free stream
+  rho = p = 1, u = (1, 1)), dt = 5 x the explicit DG limit, 8x8 subdomains.
+* ``densitywave3d`` Euler on the periodic unit cube, D3Q6, p = 1, 128^3 cells,
+  rho = 1 + 0.2 sin(2 pi (x + y + z) + phi), phi ~ U(0, 2 pi), u = (1,1,1),
+  p = 1, dt = 5 x the explicit DG limit, 16^3 subdomains.
+* ``densitywave2d`` the 2D analogue on [0,1]^2 (used by the batched mix).
+
+Kinetic speed: lambda = 1.1 d max_nodes max_a (|u_a| + c), which keeps the
+2d-velocity equilibria W/(2d) +- Q^a/(2 lambda) monotone.  Explicit DG limit
+on Cartesian Q_p cells: dt_exp = h / ((2p + 1) d a_max).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+from typing import Callable, Optional
+
+import numpy as np
+
+ADVECTION = 0
+EULER = 1
+
+# Gauss-Lobatto points on [0, 1] (closed forms; Abramowitz & Stegun 25.4.32).
+_GLL = {
+    1: (0.0, 1.0),
+    2: (0.0, 0.5, 1.0),
+    3: (0.0, 0.5 - 0.5 / math.sqrt(5.0), 0.5 + 0.5 / math.sqrt(5.0), 1.0),
+}
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    n: tuple
+    lo: tuple
+    hi: tuple
+    degree: int
+    system: int
+    lam: float
+    dt: float
+    omega: float
+    gamma: float
+    adv: tuple
+    tiles: tuple
+    iters: int
+    steps: int
+    precision: str            # "f64" or "f32"
+    W0: np.ndarray = field(repr=False)
+    exact: Optional[Callable] = field(default=None, repr=False)  # exact(t) -> W
+
+    @property
+    def m(self) -> int:
+        return 1 if self.system == ADVECTION else self.dim + 2
+
+    @property
+    def npop(self) -> int:
+        return 2 * self.dim * self.m
+
+    @property
+    def nodes(self) -> int:
+        return int(np.prod(self.n)) * (self.degree + 1) ** self.dim
+
+    @property
+    def kinetic_dofs(self) -> int:
+        return self.npop * self.nodes
+
+    def oracle_kwargs(self) -> dict:
+        return dict(dim=self.dim, n=self.n, lo=self.lo, hi=self.hi, degree=self.degree,
+                    system=self.system, lam=self.lam, dt=self.dt, omega=self.omega,
+                    gamma=self.gamma, adv=self.adv, tiles=self.tiles, iters=self.iters)
+
+
+def node_coords(dim, n, lo, hi, degree) -> np.ndarray:
+    """Node positions (nodes, dim) in storage order."""
+    xi = np.asarray(_GLL[degree])
+    axes = []
+    for a in range(dim):
+        h = (hi[a] - lo[a]) / n[a]
+        axes.append(lo[a] + (np.arange(n[a])[:, None] + xi[None, :]) * h)  # (n_a, np)
+    npn = degree + 1
+    if dim == 1:
+        return axes[0].reshape(-1, 1)
+    if dim == 2:
+        X = np.broadcast_to(axes[0][None, :, None, :], (n[1], n[0], npn, npn))
+        Y = np.broadcast_to(axes[1][:, None, :, None], (n[1], n[0], npn, npn))
+        return np.stack([X.reshape(-1), Y.reshape(-1)], axis=1)
+    X = np.broadcast_to(axes[0][None, None, :, None, None, :], (n[2], n[1], n[0], npn, npn, npn))
+    Y = np.broadcast_to(axes[1][None, :, None, None, :, None], (n[2], n[1], n[0], npn, npn, npn))
+    Z = np.broadcast_to(axes[2][:, None, None, :, None, None], (n[2], n[1], n[0], npn, npn, npn))
+    return np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
+
+
+def _euler_conserved(rho, vel, pr, gamma):
+    d = len(vel)
+    E = pr / (gamma - 1.0) + 0.5 * rho * sum(u * u for u in vel)
+    return np.stack([rho] + [rho * u for u in vel] + [E], axis=0)
+
+
+def _max_speed(rho, vel, pr, gamma):
+    c = np.sqrt(gamma * pr / rho)
+    return float(max(np.max(np.abs(u) + c) for u in vel))
+
+
+def advection1d(seed: int = 0, n: int = 256, tiles: int = 1, iters: int = 3,
+                lam: float = 2.0, a: float = 1.0, dt: Optional[float] = None,
+                omega: float = 2.0, steps: int = 100, degree: int = 1,
+                precision: str = "f64") -> Workload:
+    rng = np.random.default_rng(seed)
+    A, B = rng.uniform(0.5, 1.5, size=2)
+    h = 1.0 / n
+    if dt is None:
+        dt = 4.0 * h / lam
+    x = node_coords(1, (n,), (0.0,), (1.0,), degree)[:, 0]
+
+    def u0(xx):
+        return A * np.sin(2 * np.pi * xx) + B
+
+    def exact(t):
+        return u0((x - a * t) % 1.0)[None, :]
+
+    return Workload("advection1d", 1, (n,), (0.0,), (1.0,), degree, ADVECTION, lam, dt, omega, 1.4,
+                    (a, 0.0, 0.0), (tiles,), iters, steps, precision, u0(x)[None, :].copy(), exact)
+
+
+def _vortex_fields(X, Y, xc, yc, eps, gamma, box, uinf, vinf):
+    dx = X - xc
+    dy = Y - yc
+    dx -= box * np.round(dx / box)     # minimum image on the periodic box
+    dy -= box * np.round(dy / box)
+    r2 = dx * dx + dy * dy
+    e = np.exp(0.5 * (1.0 - r2))
+    u = uinf - eps / (2 * np.pi) * e * dy
+    v = vinf + eps / (2 * np.pi) * e * dx
+    T = 1.0 - (gamma - 1.0) * eps * eps / (8.0 * gamma * np.pi * np.pi) * e * e
+    rho = T ** (1.0 / (gamma - 1.0))
+    pr = rho ** gamma
+    return rho, (u, v), pr
+
+
+def vortex2d(seed: int = 0, n: int = 256, degree: int = 2, tiles: int = 8, iters: int = 3,
+             dt_mult: float = 5.0, omega: float = 2.0, steps: int = 200,
+             precision: str = "f32", box: float = 10.0) -> Workload:
+    rng = np.random.default_rng(seed)
+    xc, yc = rng.uniform(0.0, box, size=2)
+    eps = rng.uniform(3.0, 5.0)
+    gamma = 1.4
+    uinf, vinf = 1.0, 1.0
+    xyz = node_coords(2, (n, n), (0.0, 0.0), (box, box), degree)
+    X, Y = xyz[:, 0], xyz[:, 1]
+    rho, vel, pr = _vortex_fields(X, Y, xc, yc, eps, gamma, box, uinf, vinf)
+    amax = _max_speed(rho, vel, pr, gamma)
+    lam = 1.1 * 2 * amax
+    h = box / n
+    dt = dt_mult * h / ((2 * degree + 1) * 2 * amax)
+
+    def exact(t):
+        r, vv, p = _vortex_fields(X, Y, xc + uinf * t, yc + vinf * t, eps, gamma, box, uinf, vinf)
+        return _euler_conserved(r, vv, p, gamma)
+
+    W0 = _euler_conserved(rho, vel, pr, gamma)
+    return Workload("vortex2d", 2, (n, n), (0.0, 0.0), (box, box), degree, EULER, lam, dt, omega,
+                    gamma, (0.0, 0.0, 0.0), (tiles, tiles), iters, steps, precision, W0, exact)
+
+
+def _densitywave(dim, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision, amp=0.2):
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.0, 2 * np.pi)
+    gamma = 1.4
+    vel0 = (1.0,) * dim
+    lo, hi = (0.0,) * dim, (1.0,) * dim
+    xyz = node_coords(dim, (n,) * dim, lo, hi, degree)
+    s = xyz.sum(axis=1)
+
+    def fields(t):
+        rho = 1.0 + amp * np.sin(2 * np.pi * (s - dim * t) + phi)
+        vel = tuple(np.full_like(rho, u) for u in vel0)
+        pr = np.ones_like(rho)
+        return rho, vel, pr
+
+    rho, vel, pr = fields(0.0)
+    amax = _max_speed(rho, vel, pr, gamma)
+    lam = 1.1 * dim * amax
+    h = 1.0 / n
+    dt = dt_mult * h / ((2 * degree + 1) * dim * amax)
+
+    def exact(t):
+        r, vv, p = fields(t)
+        return _euler_conserved(r, vv, p, gamma)
+
+    return Workload(f"densitywave{dim}d", dim, (n,) * dim, lo, hi, degree, EULER, lam, dt, omega,
+                    gamma, (0.0, 0.0, 0.0), (tiles,) * dim, iters, steps, precision,
+                    _euler_conserved(rho, vel, pr, gamma), exact)
+
+
+def densitywave3d(seed: int = 0, n: int = 128, degree: int = 1, tiles: int = 16, iters: int = 3,
+                  dt_mult: float = 5.0, omega: float = 2.0, steps: int = 200,
+                  precision: str = "f32") -> Workload:
+    return _densitywave(3, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision)
+
+
+def densitywave2d(seed: int = 0, n: int = 64, degree: int = 1, tiles: int = 2, iters: int = 3,
+                  dt_mult: float = 5.0, omega: float = 2.0, steps: int = 100,
+                  precision: str = "f32") -> Workload:
+    return _densitywave(2, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision)
+
+
+def with_(w: Workload, **kw) -> Workload:
+    """Copy of a workload with some recipe fields replaced (initial data kept)."""
+    return replace(w, **kw)
+
+
+def batched_mix(seed: int = 0, count: int = 64, sizes=(64, 128, 256, 512), degrees=(1, 2, 3),
+                dt_range=(2.0, 8.0), steps: int = 100):
+    """Uneven 2D Euler/D2Q4 instances: n ~ sizes, p ~ degrees, vortex or density
+    wave 50/50, dt multiple ~ U(dt_range); subdomains of 32 cells per side."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        p = int(rng.choice(degrees))
+        mult = float(rng.uniform(*dt_range))
+        sub_seed = int(rng.integers(0, 2 ** 31 - 1))
+        tiles = max(1, n // 32)
+        if rng.uniform() < 0.5:
+            w = vortex2d(seed=sub_seed, n=n, degree=p, tiles=tiles, dt_mult=mult, steps=steps)
+        else:
+            w = densitywave2d(seed=sub_seed, n=n, degree=p, tiles=tiles, dt_mult=mult, steps=steps)
+        out.append(w)
+    return out
