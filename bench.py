@@ -1,0 +1,315 @@
+"""Benchmark of the kinetic DG step on GB300.
+
+A step is one application of S(dt) = R_omega o T_CN(dt) to the whole state:
+the K = 3 subdomain-iterated downwind DG transport of every population plus
+the fused over-relaxation, i.e. one launch of the fused step kernel.
+
+Workload (default): 2D compressible Euler, isentropic vortex on [0,10]^2,
+256 x 256 cells, DG degree 2 (3 x 3 Gauss-Lobatto nodes), D2Q4 (16
+populations per node), dt = 5 x the explicit DG limit, 8 x 8 subdomains,
+FP32 kinetic state: 9,437,184 kinetic DOF (37.7 MB).  The state is smaller
+than L2, so L2 is flushed (a 256 MB write) before every timed step and only
+the step kernel itself is inside the CUDA-event window.
+
+Metric: kinetic-DOF updates per second (one kinetic DOF = one nodal value of
+one population advanced by one full step).
+
+`--impl reference` times the FP64 CPU oracle (the test reference of this
+repository) on the same workload and metric on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "kinetic-DOF updates/s"
+UNIT = "DOF-updates/s"
+ALGO_BYTES_PER_DOF = {"f32": 8, "f64": 16}   # read f^n once + write f^{n+1} once
+
+
+def make_workload(name):
+    import workloads
+    if name == "vortex2d":
+        w = workloads.vortex2d(seed=0)
+        desc = "vortex2d-euler-256x256-p2-D2Q4-8x8sub-K3"
+    elif name == "densitywave3d":
+        w = workloads.densitywave3d(seed=0)
+        desc = "densitywave3d-euler-128^3-p1-D3Q6-16^3sub-K3"
+    elif name == "advection1d":
+        w = workloads.advection1d(seed=0, n=256, tiles=4)
+        desc = "advection1d-256-p1-D1Q2-4sub-K3"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return w, desc
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_oracle_rate(w, budget_s=12.0, max_steps=50):
+    """The oracle as it stands, single thread, timed on a bounded sample:
+    whole steps of the same workload from the same initial state."""
+    import oracle
+    P = oracle.Problem(**w.oracle_kwargs())
+    f = oracle.init(P, w.W0)
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps:
+        oracle.step(P, f, 1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return w.kinetic_dofs * steps / dt, steps, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    w, desc = make_workload(args.workload)
+    import oracle
+    P = oracle.Problem(**w.oracle_kwargs())
+    f = oracle.init(P, w.W0)
+    for _ in range(args.warmup):
+        oracle.step(P, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(P, f, 1)
+    el = time.perf_counter() - t0
+    value = w.kinetic_dofs * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "kinetic_dofs": w.kinetic_dofs, "parallelism": "cpu-1thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full steps of {desc} (after {args.warmup} warm-up)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import paper_2212_11010_gb300 as kin
+    from paper_2212_11010_gb300 import build as kbuild
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if not kbuild.up_to_date():
+        if rank == 0:
+            kbuild.build()
+        if ws > 1:
+            dist.barrier()
+    kin.load_library()
+    dev = torch.cuda.current_device()
+
+    w, desc = make_workload(args.workload)
+    prec = args.precision or w.precision
+    kprec = kin.KIN_FP32 if prec == "f32" else kin.KIN_FP64
+    stream = torch.cuda.Stream()
+    ctx = kin.Context.from_workload(w, precision=kprec, torch_alloc=True, stream=stream.cuda_stream)
+    W0 = np.ascontiguousarray(w.W0.reshape(-1))
+    ctx.set_state(W0)
+    dofs = w.kinetic_dofs
+    esize = 4 if prec == "f32" else 8
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+
+    # warm-up
+    for _ in range(args.warmup):
+        flush_l2()
+        ctx.step(1)
+    stream.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush_l2()
+            starts[i].record(stream)
+            ctx.step(1)
+            ends[i].record(stream)
+        stream.synchronize()
+        wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    times = [s.elapsed_time(e) for s, e in zip(starts, ends)]   # ms
+    local_ms = float(np.sum(times))
+    if ws > 1:
+        dist.barrier()
+        t = torch.tensor([local_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    else:
+        max_ms = local_ms
+    ms_per_step = max_ms / args.steps
+    value = ws * dofs / (ms_per_step * 1e-3)
+
+    # the same step through the public C ABI with host buffers: pinned host
+    # f -> kin_set_kinetic -> kin_step(1) -> kin_get_kinetic -> pinned host
+    fh = torch.empty(ctx.info.kinetic_values, dtype=torch.float32 if prec == "f32" else torch.float64,
+                     pin_memory=True)
+    kin.kin_get_kinetic(ctx.ctx, fh.numpy())
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        kin.kin_set_kinetic(ctx.ctx, fh.numpy())
+        ctx.step(1)
+        kin.kin_get_kinetic(ctx.ctx, fh.numpy())
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        kin.kin_set_kinetic(ctx.ctx, fh.numpy())
+        ctx.step(1)
+        kin.kin_get_kinetic(ctx.ctx, fh.numpy())
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    fbytes = ctx.info.kinetic_values * esize
+
+    peak, peak_kind = measured_peak_hbm()
+    algo_bytes = ALGO_BYTES_PER_DOF[prec] * dofs
+    achieved = algo_bytes / (ms_per_step * 1e-3) / 1e9
+    clocks = clk.summary()
+
+    # result sanity (not timed): finite state
+    Wf = ctx.get_state()
+    finite = bool(np.isfinite(Wf).all())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": desc, "kinetic_dofs": dofs, "state_bytes": fbytes,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "block": list(ctx.info.block), "grid": ctx.info.grid,
+                       "smem_bytes": ctx.info.smem_bytes,
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes},
+            "e2e": {"value": dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": fbytes,
+                    "d2h_bytes_per_step": fbytes},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "wall_s_timed_region": wall,
+            "state_finite": finite,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            rate, nst, el = cpu_oracle_rate(w)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"{nst} full steps of {desc} in {el:.1f} s"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="vortex2d",
+                    choices=["vortex2d", "densitywave3d", "advection1d"])
+    ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

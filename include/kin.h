@@ -1,0 +1,183 @@
+/*
+ * kin.h -- C ABI of the GB300 (sm_103a) kinetic DG library.
+ *
+ * The library advances the kinetic representation of a hyperbolic system of
+ * conservation laws (Gerhard, Helluy, Michel-Dansac, Weber, "Parallel kinetic
+ * schemes for conservation laws, with large time steps", arXiv:2212.11010):
+ *
+ *   one step S(dt) = R_omega o T_CN(dt)
+ *     T_CN  Crank-Nicolson implicit upwind DG transport of every population
+ *           f_k at its constant velocity V_k (Sec. 3.1, eq. dg_imp; "which we
+ *           use in practice", Sec. 3.1), solved cell by cell in downwind order
+ *           (Sec. 3.2) inside each subdomain, the subdomains coupled by the
+ *           lagged iteration of Sec. 5.1 (eq. ibvp) with K iterations;
+ *     R     W = sum_k f_k, f_k <- omega M_k(W) + (1 - omega) f_k
+ *           (Sec. 2.2, eq. over_relaxation).
+ *
+ * Meshes are periodic Cartesian boxes with tensor Gauss-Lobatto nodes
+ * (degree p, (p+1)^d nodes per cell).  Velocity sets: 2d velocities
+ * +-lambda e_a (D1Q2, D2Q4, D3Q6) with M_{a,+-} = W/(2d) +- Q^a(W)/(2 lambda),
+ * which satisfies the moment conditions of eq. maxwell_def.
+ *
+ * Storage order (host and device, every call):
+ *   W  (macroscopic)  double  [v][cz][cy][cx][nz][ny][nx]
+ *   f  (kinetic)      ctx precision (float or double)
+ *                     [pop][cz][cy][cx][nz][ny][nx],  pop = k*m + v,
+ *                     k = 2a + s: V_k = +lambda e_a (s = 0) or -lambda e_a (s = 1)
+ *   Cells are row-major with x fastest; inside a cell the x node is fastest.
+ *   m = 1 (scalar advection) or d + 2 (Euler: rho, rho u_1..rho u_d, E).
+ *
+ * Errors: every call returns a kin_status.  No exception crosses the ABI.
+ * After the first failure of a call that touched the device the context is
+ * poisoned: later calls return KIN_ESTATE until kin_destroy.  A message for
+ * the last error is available from kin_last_error().
+ *
+ * Threads: a context may be used by one host thread at a time.  Work is
+ * stream-ordered on the context's stream (kin_opts.stream).
+ */
+#ifndef KIN_H
+#define KIN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kin_ctx kin_ctx;               /* opaque, owned by the library */
+
+typedef enum {
+    KIN_OK = 0,
+    KIN_EINVAL = 1,     /* bad argument: nothing was done                     */
+    KIN_ENOMEM = 2,     /* device allocation failed                           */
+    KIN_EBUDGET = 3,    /* request exceeds kin_opts.mem_budget                */
+    KIN_ECUDA = 4,      /* a CUDA call failed (context is poisoned)           */
+    KIN_ETIMEOUT = 5,   /* a bounded device wait gave up (context poisoned)   */
+    KIN_ESTATE = 6      /* context poisoned by an earlier error, or no state  */
+} kin_status;
+
+enum { KIN_ADVECTION = 0, KIN_EULER = 1 };          /* kin_model.system   */
+enum { KIN_D1Q2 = 1, KIN_D2Q4 = 2, KIN_D3Q6 = 3 };  /* kin_model.velset   */
+enum { KIN_FP64 = 0, KIN_FP32 = 1 };                /* kin_opts.precision */
+
+/* Periodic Cartesian box [lo, hi] with n[a] cells along axis a (axes >= dim
+ * must have n = 1). */
+typedef struct {
+    int dim;
+    int n[3];
+    double lo[3];
+    double hi[3];
+} kin_mesh;
+
+/* Kinetic model.  lambda: kinetic speed |V_k| (must satisfy the
+ * sub-characteristic condition of Sec. 2.1 for the data; the library does not
+ * check it).  omega in [1, 2] (eq. over_relaxation).  gamma: Euler gas
+ * constant.  adv: advection velocity of the scalar law. */
+typedef struct {
+    int system;
+    int velset;
+    double lambda;
+    double gamma;
+    double adv[3];
+    double omega;
+} kin_model;
+
+/* Device allocator hook: called with the context's stream.  Both NULL means
+ * cudaMalloc / cudaFree. */
+typedef void* (*kin_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*kin_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* Options.  tiles[a]: number of subdomains along axis a (must divide n[a];
+ * Sec. 5.1).  iters: subdomain iterations K per step (>= 1; the paper uses 3,
+ * Sec. 5.2).  block[a]: cells per thread block along a (must divide the
+ * subdomain extent n[a]/tiles[a]; 0 = chosen by the library).  The block
+ * size changes only the schedule, never the result beyond round-off.
+ * mem_budget: upper bound in bytes on device memory the context may hold
+ * (0 = unbounded).  stream: cudaStream_t (NULL = the legacy default stream). */
+typedef struct {
+    int tiles[3];
+    int iters;
+    int precision;
+    int block[3];
+    size_t mem_budget;
+    void* stream;
+    kin_alloc_fn alloc;
+    kin_free_fn free;
+    void* alloc_user;
+} kin_opts;
+
+/* Sizes of a context. */
+typedef struct {
+    int dim, degree, m, nvel, npop, nodes_per_cell;
+    size_t cells, nodes;            /* nodes = cells * nodes_per_cell          */
+    size_t kinetic_values;          /* npop * nodes (elements of f)            */
+    size_t state_values;            /* m * nodes (elements of W)               */
+    size_t device_bytes;            /* device memory held by the context       */
+    int precision;
+    int block[3];                   /* thread-block cell extents in use        */
+    int smem_bytes;                 /* dynamic shared memory per thread block  */
+    int grid;                       /* thread blocks per step launch           */
+    long long steps_done;
+} kin_info;
+
+/* Create a context: validates arguments, computes on the GPU in FP64 the
+ * Gauss-Lobatto rule and, per velocity, the inverse of the local implicit
+ * block of eq. dg_imp (Crank-Nicolson half step tau = dt/2; Sec. 3.2 notes
+ * this preprocessing happens once), and allocates f, the interface-trace
+ * buffers of eq. ibvp and the FP64 staging buffers.  Returns KIN_EINVAL
+ * (bad mesh/model/opts, tiles not dividing n, degree outside 1..3),
+ * KIN_EBUDGET, KIN_ENOMEM or KIN_ECUDA; *out is NULL on failure. */
+kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, double dt,
+                      const kin_opts* opts, kin_ctx** out);
+
+/* Set f = M(W) at every node (Sec. 2.2: the natural initial choice
+ * F_k = M_k(W(., 0))).  W: m * nodes doubles in the storage order above, on
+ * the host (on_device = 0, pageable or pinned; copied before return) or on
+ * the device (on_device = 1, read in stream order).  n_values must equal
+ * m * nodes (else KIN_EINVAL).  Resets the step counter. */
+kin_status kin_set_state(kin_ctx* ctx, const double* W, size_t n_values, int on_device);
+
+/* Set the kinetic state f directly (checkpoint resume: after the first step
+ * f != M(W), Sec. 2.2 remark, so W alone cannot restart a run).  f holds
+ * npop * nodes values of the context precision. */
+kin_status kin_set_kinetic(kin_ctx* ctx, const void* f, size_t n_values, int on_device);
+
+/* Enqueue nsteps applications of S(dt) on the context stream and return
+ * (asynchronous).  nsteps < 0: KIN_EINVAL; no state set: KIN_ESTATE. */
+kin_status kin_step(kin_ctx* ctx, int nsteps);
+
+/* W = sum_k f_k (Sec. 2.2, step 3) into W (m * nodes doubles).  Host
+ * destination: synchronises the stream before return.  Device destination:
+ * stream-ordered. */
+kin_status kin_get_state(kin_ctx* ctx, double* W, size_t n_values, int on_device);
+
+/* Copy out the kinetic state f (npop * nodes values of the context precision). */
+kin_status kin_get_kinetic(kin_ctx* ctx, void* f, size_t n_values, int on_device);
+
+/* FP64 diagnostics, synchronous.  mass_per_var (m doubles, may be NULL): the
+ * quadrature integral of every conserved variable over the box.
+ * next_defect (m doubles, may be NULL): the mass change that the next step's
+ * finite subdomain iteration will leave at subdomain interfaces, dt |V.N|
+ * times the face integral of (trace^{K-1} - trace^{K}) summed over every
+ * upwind subdomain boundary (zero up to round-off when the iteration has
+ * converged).  iter_residual (may be NULL): max over those faces of
+ * |trace^{K} - trace^{K-1}|. */
+kin_status kin_diag(kin_ctx* ctx, double* mass_per_var, double* next_defect, double* iter_residual);
+
+/* Block the host until the context's queued work is done. */
+kin_status kin_sync(kin_ctx* ctx);
+
+kin_status kin_query(const kin_ctx* ctx, kin_info* info);
+
+/* Release every resource of the context (after synchronising its stream).
+ * NULL is accepted. */
+kin_status kin_destroy(kin_ctx* ctx);
+
+/* Message of the last error of this context (or of the last failed
+ * kin_create on this thread when ctx is NULL); never NULL. */
+const char* kin_last_error(const kin_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

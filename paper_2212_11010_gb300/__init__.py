@@ -1,0 +1,302 @@
+"""GB300 (sm_103a) kinetic DG library -- thin Python binding of include/kin.h.
+
+The functions below carry the C ABI's names and only marshal arguments
+(numpy arrays for host buffers, torch tensors for device or pinned host
+buffers); every step of the method runs in the CUDA kernels of ``libkin.so``.
+There is no CPU fallback: if the library cannot be loaded, importing a
+function raises.
+
+Method (arXiv:2212.11010): one step S(dt) = R_omega o T_CN(dt) -- an implicit
+upwind DG Crank-Nicolson transport of every kinetic population, solved by
+downwind sweeps inside subdomains coupled by the lagged iteration of Sec. 5.1,
+followed by the over-relaxation f <- omega M(W) + (1 - omega) f (Sec. 2.2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkin.so")
+
+KIN_OK, KIN_EINVAL, KIN_ENOMEM, KIN_EBUDGET, KIN_ECUDA, KIN_ETIMEOUT, KIN_ESTATE = range(7)
+KIN_ADVECTION, KIN_EULER = 0, 1
+KIN_D1Q2, KIN_D2Q4, KIN_D3Q6 = 1, 2, 3
+KIN_FP64, KIN_FP32 = 0, 1
+
+STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
+                4: "KIN_ECUDA", 5: "KIN_ETIMEOUT", 6: "KIN_ESTATE"}
+
+EXPORTED = ["kin_create", "kin_set_state", "kin_set_kinetic", "kin_step", "kin_get_state",
+            "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error"]
+
+
+class KinError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class kin_mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class kin_model(ctypes.Structure):
+    _fields_ = [("system", ctypes.c_int), ("velset", ctypes.c_int), ("lam", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 3), ("omega", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class kin_opts(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_int * 3), ("iters", ctypes.c_int), ("precision", ctypes.c_int),
+                ("block", ctypes.c_int * 3), ("mem_budget", ctypes.c_size_t),
+                ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", ctypes.c_void_p)]
+
+
+class kin_info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("m", ctypes.c_int),
+                ("nvel", ctypes.c_int), ("npop", ctypes.c_int), ("nodes_per_cell", ctypes.c_int),
+                ("cells", ctypes.c_size_t), ("nodes", ctypes.c_size_t),
+                ("kinetic_values", ctypes.c_size_t), ("state_values", ctypes.c_size_t),
+                ("device_bytes", ctypes.c_size_t), ("precision", ctypes.c_int),
+                ("block", ctypes.c_int * 3), ("smem_bytes", ctypes.c_int), ("grid", ctypes.c_int),
+                ("steps_done", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libkin.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    sz = ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.kin_create.argtypes = [ctypes.POINTER(kin_mesh), ctypes.POINTER(kin_model), ctypes.c_int,
+                               ctypes.c_double, ctypes.POINTER(kin_opts), ctypes.POINTER(vp)]
+    lib.kin_set_state.argtypes = [vp, vp, sz, ctypes.c_int]
+    lib.kin_set_kinetic.argtypes = [vp, vp, sz, ctypes.c_int]
+    lib.kin_step.argtypes = [vp, ctypes.c_int]
+    lib.kin_get_state.argtypes = [vp, vp, sz, ctypes.c_int]
+    lib.kin_get_kinetic.argtypes = [vp, vp, sz, ctypes.c_int]
+    lib.kin_diag.argtypes = [vp, dp, dp, dp]
+    lib.kin_sync.argtypes = [vp]
+    lib.kin_query.argtypes = [vp, ctypes.POINTER(kin_info)]
+    lib.kin_destroy.argtypes = [vp]
+    lib.kin_last_error.argtypes = [vp]
+    lib.kin_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name != "kin_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status):
+    if status != KIN_OK:
+        msg = load_library().kin_last_error(ctx).decode()
+        raise KinError(status, msg)
+
+
+def _ptr(buf):
+    """(pointer, on_device) of a numpy array or torch tensor (contiguous)."""
+    if isinstance(buf, np.ndarray):
+        assert buf.flags.c_contiguous
+        return buf.ctypes.data, 0
+    import torch
+    assert isinstance(buf, torch.Tensor) and buf.is_contiguous()
+    return buf.data_ptr(), 1 if buf.is_cuda else 0
+
+
+# torch caching-allocator hooks (PyTorch owns the device memory)
+_hooks = {}
+
+
+def torch_allocator_hooks(device=None):
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    if dev in _hooks:
+        return _hooks[dev]
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _hooks[dev] = (ALLOC_FN(_alloc), FREE_FN(_free))
+    return _hooks[dev]
+
+
+# ---------------------------------------------------------------------------
+# C ABI, same names
+# ---------------------------------------------------------------------------
+
+def kin_create(mesh: kin_mesh, model: kin_model, degree: int, dt: float, opts: kin_opts):
+    lib = load_library()
+    ctx = ctypes.c_void_p()
+    st = lib.kin_create(ctypes.byref(mesh), ctypes.byref(model), degree, dt, ctypes.byref(opts),
+                        ctypes.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def kin_set_state(ctx, W, n_values=None):
+    p, dev = _ptr(W)
+    n = W.size if isinstance(W, np.ndarray) else W.numel()
+    _check(ctx, load_library().kin_set_state(ctx, p, n if n_values is None else n_values, dev))
+
+
+def kin_set_kinetic(ctx, f, n_values=None):
+    p, dev = _ptr(f)
+    n = f.size if isinstance(f, np.ndarray) else f.numel()
+    _check(ctx, load_library().kin_set_kinetic(ctx, p, n if n_values is None else n_values, dev))
+
+
+def kin_step(ctx, nsteps: int):
+    _check(ctx, load_library().kin_step(ctx, nsteps))
+
+
+def kin_get_state(ctx, W, n_values=None):
+    p, dev = _ptr(W)
+    n = W.size if isinstance(W, np.ndarray) else W.numel()
+    _check(ctx, load_library().kin_get_state(ctx, p, n if n_values is None else n_values, dev))
+
+
+def kin_get_kinetic(ctx, f, n_values=None):
+    p, dev = _ptr(f)
+    n = f.size if isinstance(f, np.ndarray) else f.numel()
+    _check(ctx, load_library().kin_get_kinetic(ctx, p, n if n_values is None else n_values, dev))
+
+
+def kin_diag(ctx, m: int):
+    mass = np.zeros(m)
+    defect = np.zeros(m)
+    resid = np.zeros(1)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(ctx, load_library().kin_diag(ctx, mass.ctypes.data_as(dp), defect.ctypes.data_as(dp),
+                                        resid.ctypes.data_as(dp)))
+    return mass, defect, float(resid[0])
+
+
+def kin_sync(ctx):
+    _check(ctx, load_library().kin_sync(ctx))
+
+
+def kin_query(ctx) -> kin_info:
+    info = kin_info()
+    _check(ctx, load_library().kin_query(ctx, ctypes.byref(info)))
+    return info
+
+
+def kin_destroy(ctx):
+    _check(None, load_library().kin_destroy(ctx))
+
+
+def kin_last_error(ctx=None) -> str:
+    return load_library().kin_last_error(ctx).decode()
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 0.0),
+              tiles=(1, 1, 1), iters=3, precision=KIN_FP64, block=(0, 0, 0), mem_budget=0,
+              stream=None, torch_alloc=False):
+    pad = lambda t, fill: tuple(t) + (fill,) * (3 - len(tuple(t)))
+    mesh = kin_mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
+                    (ctypes.c_double * 3)(*pad(hi, 1.0)))
+    model = kin_model(system, dim, lam, gamma, (ctypes.c_double * 3)(*pad(adv, 0.0)), omega)
+    opts = kin_opts()
+    opts.tiles = (ctypes.c_int * 3)(*pad(tiles, 1))
+    opts.iters = iters
+    opts.precision = precision
+    opts.block = (ctypes.c_int * 3)(*pad(block, 0))
+    opts.mem_budget = mem_budget
+    opts.stream = stream
+    if torch_alloc:
+        a, f = torch_allocator_hooks()
+        opts.alloc = a
+        opts.free = f
+    return mesh, model, opts
+
+
+class Context:
+    """Owning wrapper of a kin_ctx (create / destroy); the methods call the
+    C ABI functions above."""
+
+    def __init__(self, dim, n, lo, hi, degree, system, lam, dt, **kw):
+        self.mesh, self.model, self.opts = make_args(dim, n, lo, hi, system, lam, **kw)
+        self.ctx = kin_create(self.mesh, self.model, degree, dt, self.opts)
+        self.info = kin_query(self.ctx)
+
+    @classmethod
+    def from_workload(cls, w, precision=None, **kw):
+        prec = precision if precision is not None else (KIN_FP32 if w.precision == "f32" else KIN_FP64)
+        return cls(w.dim, w.n, w.lo, w.hi, w.degree, w.system, w.lam, w.dt, omega=w.omega,
+                   gamma=w.gamma, adv=w.adv, tiles=w.tiles, iters=w.iters, precision=prec, **kw)
+
+    @property
+    def dtype(self):
+        return np.float32 if self.info.precision == KIN_FP32 else np.float64
+
+    def set_state(self, W):
+        kin_set_state(self.ctx, W)
+
+    def set_kinetic(self, f):
+        kin_set_kinetic(self.ctx, f)
+
+    def step(self, n=1):
+        kin_step(self.ctx, n)
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros(self.info.state_values)
+        kin_get_state(self.ctx, out)
+        return out
+
+    def get_kinetic(self, out=None):
+        if out is None:
+            out = np.zeros(self.info.kinetic_values, dtype=self.dtype)
+        kin_get_kinetic(self.ctx, out)
+        return out
+
+    def diag(self):
+        return kin_diag(self.ctx, self.info.m)
+
+    def sync(self):
+        kin_sync(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            kin_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,590 @@
+// kin_api.cu -- the C ABI (include/kin.h): argument validation, device
+// memory, launch configuration and stream ordering.  Every step of the
+// method runs in the kernels of kin_device.cuh / kin_aux.cu.
+#include "../../include/kin.h"
+#include "kin_aux.h"
+#include "kin_device.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace kin;
+
+struct kin_ctx {
+    // problem
+    int dim = 1, n[3] = {1, 1, 1}, degree = 1, system = 0, m = 1, nvel = 2, npop = 2, NP = 2, NN = 2;
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
+    double lambda = 1, gamma = 1.4, adv[3] = {0, 0, 0}, omega = 2, dt = 0;
+    int tiles[3] = {1, 1, 1}, L[3] = {1, 1, 1}, iters = 3, precision = KIN_FP64;
+    int B[3] = {1, 1, 1}, nblk[3] = {1, 1, 1}, nb[3] = {1, 1, 1};
+    size_t cells = 0, nodes = 0, sig_stride = 0, esize = 8;
+    // runtime
+    cudaStream_t stream = nullptr;
+    kin_alloc_fn alloc = nullptr;
+    kin_free_fn dealloc = nullptr;
+    void* alloc_user = nullptr;
+    size_t budget = 0, bytes_held = 0;
+    std::vector<std::pair<void*, size_t>> blocks;
+    void* f = nullptr;
+    void* sig[2] = {nullptr, nullptr};
+    void* raw[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* c64 = nullptr;
+    void* coef = nullptr;
+    double* gll = nullptr;
+    double* Wbuf = nullptr;
+    double* partial = nullptr;
+    double* result = nullptr;
+    StepKernel kfn = nullptr;
+    int smem = 0, grid = 0;
+    bool have_state = false;
+    long long steps_done = 0;
+    bool poisoned = false;
+    std::string err;
+};
+
+static thread_local std::string g_create_error = "no error";
+
+static kin_status fail(kin_ctx* c, kin_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->err = buf;
+        if (st == KIN_ECUDA || st == KIN_ETIMEOUT) c->poisoned = true;
+    } else {
+        g_create_error = buf;
+    }
+    return st;
+}
+
+#define KIN_CUDA(c, call)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail((c), KIN_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static kin_status dev_alloc(kin_ctx* c, size_t bytes, void** out)
+{
+    *out = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (c->budget && c->bytes_held + bytes > c->budget)
+        return fail(c, KIN_EBUDGET, "device memory budget of %zu bytes exceeded (%zu held, %zu asked)",
+                    c->budget, c->bytes_held, bytes);
+    void* p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, (void*)c->stream, c->alloc_user);
+        if (!p) return fail(c, KIN_ENOMEM, "allocator hook returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, KIN_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    c->blocks.push_back({p, bytes});
+    c->bytes_held += bytes;
+    *out = p;
+    return KIN_OK;
+}
+
+static void release_all(kin_ctx* c)
+{
+    for (auto& b : c->blocks) {
+        if (c->dealloc) c->dealloc(b.first, b.second, (void*)c->stream, c->alloc_user);
+        else cudaFree(b.first);
+    }
+    c->blocks.clear();
+    c->bytes_held = 0;
+}
+
+static StepKernel pick_kernel(int dim, int degree, int system, int prec)
+{
+    switch (dim) {
+    case 1: return step_kernel_d1(degree, system, prec);
+    case 2: return step_kernel_d2(degree, system, prec);
+    case 3: return step_kernel_d3(degree, system, prec);
+    default: return nullptr;
+    }
+}
+
+static size_t block_smem(const kin_ctx* c, const int B[3])
+{
+    return (size_t)c->npop * B[0] * B[1] * B[2] * c->NN * c->esize;
+}
+
+// Largest divisor of L that is smaller than b (at least 1).
+static int next_divisor_below(int L, int b)
+{
+    for (int d = b - 1; d >= 1; --d)
+        if (L % d == 0) return d;
+    return 1;
+}
+
+// Default cell block: start from the whole subdomain and shrink the longest
+// extent until the block fits the shared-memory target and the grid has
+// enough blocks to fill 152 SMs twice.
+static void choose_block(const kin_ctx* c, int B[3])
+{
+    const size_t target = 64 * 1024;
+    for (int a = 0; a < 3; ++a) B[a] = c->L[a];
+    auto grid_of = [&](const int* b) {
+        long long g = 1;
+        for (int a = 0; a < c->dim; ++a) g *= c->n[a] / b[a];
+        return g;
+    };
+    for (int guard = 0; guard < 64; ++guard) {
+        bool too_big = block_smem(c, B) > target;
+        bool too_few = grid_of(B) < 2 * 152;
+        if (!too_big && !too_few) break;
+        int best = -1;
+        for (int a = 0; a < c->dim; ++a)
+            if (B[a] > 1 && (best < 0 || B[a] > B[best])) best = a;
+        if (best < 0) break;
+        if (!too_big && B[best] <= 4) break;     // keep lines reasonably long
+        B[best] = next_divisor_below(c->L[best], B[best]);
+    }
+}
+
+static Inst make_inst(const kin_ctx* c, int mode)
+{
+    Inst I;
+    memset(&I, 0, sizeof I);
+    I.f = c->f;
+    I.sig_in = c->sig[c->cur];
+    I.raw_in = c->raw[c->cur];
+    I.sig_out = c->sig[c->cur ^ 1];
+    I.raw_out = c->raw[c->cur ^ 1];
+    I.coef = c->coef;
+    I.nodes = (long long)c->nodes;
+    I.sig_stride = (long long)c->sig_stride;
+    for (int a = 0; a < 3; ++a) {
+        I.n[a] = c->n[a];
+        I.B[a] = c->B[a];
+        I.nblk[a] = c->nblk[a];
+        I.nb[a] = c->nb[a];
+        I.NS[a] = c->tiles[a];
+        I.adv[a] = c->adv[a];
+    }
+    I.iters = c->iters;
+    I.mode = mode;
+    I.lambda = c->lambda;
+    I.gamma = c->gamma;
+    I.omega = c->omega;
+    return I;
+}
+
+// Launch of the fused kernel: mode 0 = one full step, mode 1 = block
+// summaries of the current state only.  Flips the summary buffers.
+static kin_status launch_step(kin_ctx* c, int mode)
+{
+    Inst I = make_inst(c, mode);
+    void* args[] = {&I};
+    KIN_CUDA(c, cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(kThreads), args,
+                                 (size_t)c->smem, c->stream));
+    c->cur ^= 1;
+    return KIN_OK;
+}
+
+static PointArgs point_args(const kin_ctx* c)
+{
+    PointArgs p;
+    memset(&p, 0, sizeof p);
+    p.dim = c->dim;
+    p.degree = c->degree;
+    p.m = c->m;
+    p.system = c->system;
+    p.nodes = (long long)c->nodes;
+    p.lambda = c->lambda;
+    p.gamma = c->gamma;
+    for (int a = 0; a < 3; ++a) {
+        p.adv[a] = c->adv[a];
+        p.h[a] = c->h[a];
+    }
+    return p;
+}
+
+static kin_status check_usable(const kin_ctx* c)
+{
+    if (!c) return KIN_EINVAL;
+    if (c->poisoned) return KIN_ESTATE;
+    return KIN_OK;
+}
+
+extern "C" {
+
+kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, double dt,
+                      const kin_opts* opts, kin_ctx** out)
+{
+    if (!out) return fail(nullptr, KIN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mesh || !model || !opts) return fail(nullptr, KIN_EINVAL, "mesh, model and opts are required");
+    if (mesh->dim < 1 || mesh->dim > 3) return fail(nullptr, KIN_EINVAL, "dim must be 1..3");
+    if (degree < 1 || degree > 3) return fail(nullptr, KIN_EINVAL, "degree must be 1..3");
+    if (model->system != KIN_ADVECTION && model->system != KIN_EULER)
+        return fail(nullptr, KIN_EINVAL, "unknown system %d", model->system);
+    if (model->velset != mesh->dim)
+        return fail(nullptr, KIN_EINVAL, "velocity set D%dQ%d does not match dim %d",
+                    model->velset, 2 * model->velset, mesh->dim);
+    if (!(model->lambda > 0) || !(dt > 0))
+        return fail(nullptr, KIN_EINVAL, "lambda and dt must be positive");
+    if (!(model->omega >= 1.0 && model->omega <= 2.0))
+        return fail(nullptr, KIN_EINVAL, "omega must lie in [1, 2]");
+    if (model->system == KIN_EULER && !(model->gamma > 1.0))
+        return fail(nullptr, KIN_EINVAL, "gamma must exceed 1");
+    if (opts->iters < 1) return fail(nullptr, KIN_EINVAL, "iters must be >= 1");
+    if (opts->precision != KIN_FP64 && opts->precision != KIN_FP32)
+        return fail(nullptr, KIN_EINVAL, "unknown precision %d", opts->precision);
+    if ((opts->alloc == nullptr) != (opts->free == nullptr))
+        return fail(nullptr, KIN_EINVAL, "alloc and free hooks must be given together");
+
+    kin_ctx* c = new (std::nothrow) kin_ctx();
+    if (!c) return fail(nullptr, KIN_ENOMEM, "host allocation failed");
+    c->dim = mesh->dim;
+    c->degree = degree;
+    c->system = model->system;
+    c->m = model->system == KIN_EULER ? mesh->dim + 2 : 1;
+    c->nvel = 2 * mesh->dim;
+    c->npop = c->nvel * c->m;
+    c->NP = degree + 1;
+    c->NN = 1;
+    for (int a = 0; a < c->dim; ++a) c->NN *= c->NP;
+    c->lambda = model->lambda;
+    c->gamma = model->gamma;
+    c->omega = model->omega;
+    c->dt = dt;
+    c->iters = opts->iters;
+    c->precision = opts->precision;
+    c->esize = opts->precision == KIN_FP32 ? 4 : 8;
+    c->stream = (cudaStream_t)opts->stream;
+    c->alloc = opts->alloc;
+    c->dealloc = opts->free;
+    c->alloc_user = opts->alloc_user;
+    c->budget = opts->mem_budget;
+    c->cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        c->adv[a] = model->adv[a];
+        if (a < c->dim) {
+            if (mesh->n[a] < 1 || !(mesh->hi[a] > mesh->lo[a])) {
+                delete c;
+                return fail(nullptr, KIN_EINVAL, "axis %d: need n >= 1 and hi > lo", a);
+            }
+            if (opts->tiles[a] < 1 || mesh->n[a] % opts->tiles[a]) {
+                delete c;
+                return fail(nullptr, KIN_EINVAL, "axis %d: tiles %d must divide n %d", a,
+                            opts->tiles[a], mesh->n[a]);
+            }
+            c->n[a] = mesh->n[a];
+            c->lo[a] = mesh->lo[a];
+            c->hi[a] = mesh->hi[a];
+            c->h[a] = (mesh->hi[a] - mesh->lo[a]) / mesh->n[a];
+            c->tiles[a] = opts->tiles[a];
+            c->L[a] = c->n[a] / c->tiles[a];
+        } else {
+            if (mesh->n[a] > 1) {
+                delete c;
+                return fail(nullptr, KIN_EINVAL, "axis %d beyond dim must have n = 1", a);
+            }
+            c->n[a] = 1;
+            c->tiles[a] = 1;
+            c->L[a] = 1;
+        }
+        c->cells *= c->n[a];
+    }
+    c->nodes = c->cells * c->NN;
+
+    // cell block
+    bool user_block = opts->block[0] || opts->block[1] || opts->block[2];
+    if (user_block) {
+        for (int a = 0; a < 3; ++a) {
+            int b = a < c->dim ? opts->block[a] : 1;
+            if (b < 1 || c->L[a] % b) {
+                delete c;
+                return fail(nullptr, KIN_EINVAL, "axis %d: block %d must divide the subdomain extent %d",
+                            a, b, c->L[a]);
+            }
+            c->B[a] = b;
+        }
+    } else {
+        choose_block(c, c->B);
+    }
+    for (int a = 0; a < 3; ++a) {
+        c->nblk[a] = c->n[a] / c->B[a];
+        c->nb[a] = c->L[a] / c->B[a];
+    }
+    size_t smem = block_smem(c, c->B);
+    if (smem > 227 * 1024) {
+        delete c;
+        return fail(nullptr, KIN_EINVAL, "cell block needs %zu bytes of shared memory (> 227 KB)", smem);
+    }
+    c->smem = (int)smem;
+    c->grid = c->nblk[0] * c->nblk[1] * c->nblk[2];
+    c->kfn = pick_kernel(c->dim, degree, c->system, c->precision);
+    if (!c->kfn) {
+        delete c;
+        return fail(nullptr, KIN_EINVAL, "no kernel for dim %d degree %d", mesh->dim, degree);
+    }
+
+    // summaries: per population, n[a]/B[a] blocks x (cells / n[a]) x NP^{d-1} lines
+    size_t tn = 1;
+    for (int a = 1; a < c->dim; ++a) tn *= c->NP;
+    size_t stride = 0;
+    for (int a = 0; a < c->dim; ++a)
+        stride = std::max(stride, (size_t)c->nblk[a] * (c->cells / c->n[a]) * tn);
+    c->sig_stride = stride;
+
+    kin_status st;
+    const size_t fbytes = c->nodes * c->npop * c->esize;
+    const size_t sbytes = stride * c->npop * c->esize;
+    void* p;
+#define ALLOC(dst, bytes)                                                 \
+    do {                                                                  \
+        st = dev_alloc(c, (bytes), &p);                                   \
+        if (st != KIN_OK) {                                               \
+            g_create_error = c->err;                                      \
+            release_all(c);                                               \
+            delete c;                                                     \
+            return st;                                                    \
+        }                                                                 \
+        dst = (decltype(dst))p;                                           \
+    } while (0)
+    ALLOC(c->f, fbytes);
+    for (int i = 0; i < 2; ++i) {
+        ALLOC(c->sig[i], sbytes);
+        ALLOC(c->raw[i], sbytes);
+    }
+    ALLOC(c->c64, sizeof(double) * 6 * kCoefStride);
+    ALLOC(c->coef, c->esize == 4 ? sizeof(float) * 6 * kCoefStride : 16);
+    ALLOC(c->gll, sizeof(double) * 2 * kMaxNP);
+    ALLOC(c->Wbuf, sizeof(double) * c->m * c->nodes);
+    ALLOC(c->partial, sizeof(double) * kDiagBlocks * 6);
+    ALLOC(c->result, sizeof(double) * 8);
+#undef ALLOC
+    if (c->esize == 8) c->coef = c->c64;
+
+    if (c->smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)c->kfn,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("cudaFuncSetAttribute failed: ") + cudaGetErrorString(e);
+            release_all(c);
+            delete c;
+            return KIN_ECUDA;
+        }
+    }
+
+    SetupArgs sa;
+    memset(&sa, 0, sizeof sa);
+    sa.dim = c->dim;
+    sa.degree = degree;
+    sa.lambda = c->lambda;
+    sa.dt = dt;
+    for (int a = 0; a < 3; ++a) {
+        sa.h[a] = c->h[a];
+        sa.B[a] = c->B[a];
+    }
+    sa.c64 = c->c64;
+    sa.c32 = c->esize == 4 ? (float*)c->coef : nullptr;
+    sa.gll = c->gll;
+    cudaError_t e = launch_setup(sa, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("setup kernel failed: ") + cudaGetErrorString(e);
+        release_all(c);
+        delete c;
+        return KIN_ECUDA;
+    }
+    *out = c;
+    return KIN_OK;
+}
+
+kin_status kin_set_state(kin_ctx* c, const double* W, size_t n_values, int on_device)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (!W) return fail(c, KIN_EINVAL, "W is NULL");
+    if (n_values != (size_t)c->m * c->nodes)
+        return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->m * c->nodes, n_values);
+    const double* src = W;
+    if (!on_device) {
+        KIN_CUDA(c, cudaMemcpyAsync(c->Wbuf, W, n_values * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream));
+        src = c->Wbuf;
+    }
+    KIN_CUDA(c, launch_init(point_args(c), src, c->f, c->precision == KIN_FP32, c->stream));
+    st = launch_step(c, 1);
+    if (st) return st;
+    if (!on_device) KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_state = true;
+    c->steps_done = 0;
+    return KIN_OK;
+}
+
+kin_status kin_set_kinetic(kin_ctx* c, const void* f, size_t n_values, int on_device)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (!f) return fail(c, KIN_EINVAL, "f is NULL");
+    if (n_values != (size_t)c->npop * c->nodes)
+        return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
+    KIN_CUDA(c, cudaMemcpyAsync(c->f, f, n_values * c->esize,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    st = launch_step(c, 1);
+    if (st) return st;
+    if (!on_device) KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_state = true;
+    return KIN_OK;
+}
+
+kin_status kin_step(kin_ctx* c, int nsteps)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (nsteps < 0) return fail(c, KIN_EINVAL, "nsteps must be >= 0");
+    if (!c->have_state) return fail(c, KIN_ESTATE, "no state: call kin_set_state or kin_set_kinetic first");
+    for (int s = 0; s < nsteps; ++s) {
+        st = launch_step(c, 0);
+        if (st) return st;
+        c->steps_done++;
+    }
+    return KIN_OK;
+}
+
+kin_status kin_get_state(kin_ctx* c, double* W, size_t n_values, int on_device)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (!W) return fail(c, KIN_EINVAL, "W is NULL");
+    if (n_values != (size_t)c->m * c->nodes)
+        return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->m * c->nodes, n_values);
+    if (!c->have_state) return fail(c, KIN_ESTATE, "no state has been set");
+    double* dst = on_device ? W : c->Wbuf;
+    KIN_CUDA(c, launch_moments(point_args(c), c->f, dst, c->precision == KIN_FP32, c->stream));
+    if (!on_device) {
+        KIN_CUDA(c, cudaMemcpyAsync(W, c->Wbuf, n_values * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return KIN_OK;
+}
+
+kin_status kin_get_kinetic(kin_ctx* c, void* f, size_t n_values, int on_device)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (!f) return fail(c, KIN_EINVAL, "f is NULL");
+    if (n_values != (size_t)c->npop * c->nodes)
+        return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
+    if (!c->have_state) return fail(c, KIN_ESTATE, "no state has been set");
+    KIN_CUDA(c, cudaMemcpyAsync(f, c->f, n_values * c->esize,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KIN_OK;
+}
+
+kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, double* iter_residual)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (!c->have_state) return fail(c, KIN_ESTATE, "no state has been set");
+    double host[8] = {0};
+    if (mass_per_var) {
+        KIN_CUDA(c, launch_mass(point_args(c), c->f, c->gll, c->partial, c->result,
+                                c->precision == KIN_FP32, c->stream));
+        KIN_CUDA(c, cudaMemcpyAsync(host, c->result, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
+        KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (int v = 0; v < c->m; ++v) mass_per_var[v] = host[v];
+    }
+    if (next_defect || iter_residual) {
+        DefectArgs da;
+        memset(&da, 0, sizeof da);
+        da.dim = c->dim;
+        da.degree = c->degree;
+        da.m = c->m;
+        da.iters = c->iters;
+        da.sig_stride = (long long)c->sig_stride;
+        da.dt = c->dt;
+        da.lambda = c->lambda;
+        long long tn = 1;
+        for (int a = 1; a < c->dim; ++a) tn *= c->NP;
+        for (int a = 0; a < 3; ++a) {
+            da.h[a] = c->h[a];
+            da.nb[a] = c->nb[a];
+            da.NS[a] = c->tiles[a];
+            da.glines[a] = a < c->dim ? (long long)(c->cells / c->n[a]) * tn : 0;
+        }
+        da.total = 0;
+        for (int pop = 0; pop < c->npop; ++pop) {
+            int a = (pop / c->m) / 2;
+            da.per_pop[pop] = (long long)c->tiles[a] * da.glines[a];
+            da.total += da.per_pop[pop];
+        }
+        KIN_CUDA(c, launch_defect(da, c->sig[c->cur], c->raw[c->cur], c->c64, c->gll, c->partial,
+                                  c->result, c->precision == KIN_FP32, c->stream));
+        KIN_CUDA(c, cudaMemcpyAsync(host, c->result, sizeof(double) * 6, cudaMemcpyDeviceToHost, c->stream));
+        KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (next_defect)
+            for (int v = 0; v < c->m; ++v) next_defect[v] = host[v];
+        if (iter_residual) *iter_residual = host[5];
+    }
+    return KIN_OK;
+}
+
+kin_status kin_sync(kin_ctx* c)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+    return KIN_OK;
+}
+
+kin_status kin_query(const kin_ctx* c, kin_info* info)
+{
+    if (!c || !info) return KIN_EINVAL;
+    memset(info, 0, sizeof *info);
+    info->dim = c->dim;
+    info->degree = c->degree;
+    info->m = c->m;
+    info->nvel = c->nvel;
+    info->npop = c->npop;
+    info->nodes_per_cell = c->NN;
+    info->cells = c->cells;
+    info->nodes = c->nodes;
+    info->kinetic_values = (size_t)c->npop * c->nodes;
+    info->state_values = (size_t)c->m * c->nodes;
+    info->device_bytes = c->bytes_held;
+    info->precision = c->precision;
+    for (int a = 0; a < 3; ++a) info->block[a] = c->B[a];
+    info->smem_bytes = c->smem;
+    info->grid = c->grid;
+    info->steps_done = c->steps_done;
+    return KIN_OK;
+}
+
+kin_status kin_destroy(kin_ctx* c)
+{
+    if (!c) return KIN_OK;
+    cudaStreamSynchronize(c->stream);
+    release_all(c);
+    delete c;
+    return KIN_OK;
+}
+
+const char* kin_last_error(const kin_ctx* c)
+{
+    if (!c) return g_create_error.c_str();
+    return c->err.empty() ? "no error" : c->err.c_str();
+}
+
+}  // extern "C"

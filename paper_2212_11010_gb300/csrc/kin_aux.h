@@ -1,0 +1,59 @@
+// kin_aux.h -- internal launch interface between the C ABI layer and the
+// kernels (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace kin {
+
+constexpr int kMaxNP = 4;          // degree <= 3
+constexpr int kDiagBlocks = 304;   // 2 x 152 SMs
+
+struct Inst;
+
+struct SetupArgs {
+    int dim, degree;
+    double lambda, dt;
+    double h[3];
+    int B[3];
+    double* c64;    // [2*dim][kCoefStride] FP64 coefficients
+    float* c32;     // same, rounded to FP32 (NULL for an FP64 context)
+    double* gll;    // xi[kMaxNP], w[kMaxNP]
+};
+
+struct PointArgs {
+    int dim, degree, m, system;
+    long long nodes;
+    double lambda, gamma;
+    double adv[3];
+    double h[3];
+};
+
+struct DefectArgs {
+    int dim, degree, m, iters;
+    long long total;         // sum of per_pop
+    long long per_pop[30];   // NS[a] * glines[a] for the population's axis
+    long long glines[3];
+    long long sig_stride;
+    int nb[3], NS[3];
+    double dt, lambda;
+    double h[3];
+};
+
+typedef void (*StepKernel)(Inst);
+
+cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st);
+cudaError_t launch_init(const PointArgs& a, const double* W, void* f, int prec, cudaStream_t st);
+cudaError_t launch_moments(const PointArgs& a, const void* f, double* W, int prec, cudaStream_t st);
+cudaError_t launch_mass(const PointArgs& a, const void* f, const double* gll, double* partial,
+                        double* out, int prec, cudaStream_t st);
+cudaError_t launch_defect(const DefectArgs& a, const void* sig, const void* raw, const double* c64,
+                          const double* gll, double* partial, double* out, int prec,
+                          cudaStream_t st);
+
+// Step kernels, one translation unit per space dimension.
+StepKernel step_kernel_d1(int degree, int system, int prec);
+StepKernel step_kernel_d2(int degree, int system, int prec);
+StepKernel step_kernel_d3(int degree, int system, int prec);
+
+}  // namespace kin

@@ -1,0 +1,265 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances: FP64 kernels 1e-12 relative; FP32 kernels 1e-5 relative (GLL
+weighted L2 and max norm, per conserved variable, relative to the oracle's
+norm of that variable).  Sizes span several thread blocks and several
+subdomains; time steps are large enough that the subdomain coupling of
+eq. ibvp changes the result well above round-off.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def kin():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_11010_gb300 import build
+    build.build()
+    import paper_2212_11010_gb300 as kin
+    kin.load_library()
+    return kin
+
+
+def oracle_run(w, steps):
+    P = oracle.Problem(**w.oracle_kwargs())
+    f = oracle.init(P, w.W0)
+    oracle.step(P, f, steps)
+    return f, oracle.moments(P, f)
+
+
+def weights(w):
+    xi, wq = oracle.gll(w.degree)
+    cellw = np.ones(1)
+    for _ in range(w.dim):
+        cellw = np.kron(wq, cellw)
+    return np.tile(cellw, int(np.prod(w.n)))
+
+
+def rel_errors(w, W, Wo):
+    W = W.reshape(w.m, -1)
+    Wo = Wo.reshape(w.m, -1)
+    q = weights(w)
+    l2 = max(np.sqrt(np.sum(q * (W[v] - Wo[v]) ** 2) / np.sum(q * Wo[v] ** 2)) for v in range(w.m))
+    linf = max(np.abs(W[v] - Wo[v]).max() / np.abs(Wo[v]).max() for v in range(w.m))
+    return l2, linf
+
+
+def gpu_run(kin, w, steps, precision=None, block=(0, 0, 0)):
+    with kin.Context.from_workload(w, precision=precision, block=block) as ctx:
+        ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+        ctx.step(steps)
+        return ctx.get_state(), ctx.get_kinetic(), ctx.info
+
+
+SMALL_CASES = [
+    # (workload, block)
+    (lambda: workloads.advection1d(seed=0, n=48, tiles=4, dt=0.1), (4,)),
+    (lambda: workloads.advection1d(seed=1, n=40, tiles=1, dt=0.3, iters=2), (8,)),
+    (lambda: workloads.advection1d(seed=2, n=36, tiles=3, dt=0.15, degree=3, iters=1), (12,)),
+    (lambda: workloads.vortex2d(seed=1, n=16, degree=2, tiles=2, dt_mult=40.0), (4, 8)),
+    (lambda: workloads.vortex2d(seed=2, n=12, degree=1, tiles=(3, 1), dt_mult=30.0), (2, 6)),
+    (lambda: workloads.vortex2d(seed=3, n=8, degree=3, tiles=(1, 2), dt_mult=30.0, iters=2), (8, 2)),
+    (lambda: workloads.densitywave3d(seed=0, n=8, degree=1, tiles=2, dt_mult=30.0), (2, 2, 4)),
+    (lambda: workloads.densitywave3d(seed=1, n=6, degree=2, tiles=(3, 1, 2), dt_mult=20.0), (1, 3, 3)),
+    (lambda: workloads.with_(workloads.densitywave2d(seed=5, n=12, degree=2, tiles=3, dt_mult=20.0),
+                             omega=1.6), (2, 4)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SMALL_CASES)))
+def test_fp64_matches_oracle(kin, case):
+    make, block = SMALL_CASES[case]
+    w = make()
+    steps = 5
+    W, f, _ = gpu_run(kin, w, steps, precision=kin.KIN_FP64, block=block)
+    fo, Wo = oracle_run(w, steps)
+    assert np.abs(f - fo).max() / np.abs(fo).max() < TOL64
+    l2, linf = rel_errors(w, W, Wo)
+    assert linf < TOL64 and l2 < TOL64
+
+
+@pytest.mark.parametrize("case", range(len(SMALL_CASES)))
+def test_fp32_matches_oracle(kin, case):
+    make, block = SMALL_CASES[case]
+    w = make()
+    steps = 5
+    W, _, _ = gpu_run(kin, w, steps, precision=kin.KIN_FP32, block=block)
+    _, Wo = oracle_run(w, steps)
+    l2, linf = rel_errors(w, W, Wo)
+    assert l2 < TOL32 and linf < TOL32, (l2, linf)
+
+
+def test_subdomain_iteration_count_matters_and_matches(kin):
+    # at a large time step K = 1, 2, 3 give different results; each matches
+    # the oracle with the same K
+    base = workloads.vortex2d(seed=4, n=16, degree=2, tiles=4, dt_mult=60.0, precision="f64")
+    outs = []
+    for K in (1, 2, 3):
+        w = workloads.with_(base, iters=K, tiles=(4, 4))
+        W, _, _ = gpu_run(kin, w, 3, block=(2, 2))
+        _, Wo = oracle_run(w, 3)
+        assert np.abs(W - Wo).max() / np.abs(Wo).max() < TOL64
+        outs.append(W)
+    assert np.abs(outs[0] - outs[2]).max() > 1e-6
+    assert np.abs(outs[1] - outs[2]).max() > 1e-9
+
+
+def test_advection_1d_config(kin):
+    # 256 cells, p = 1, lambda = 2, dt = 4h/lambda, 100 steps, FP64; 1 then 4 subdomains
+    for tiles in (1, 4):
+        for seed in (0, 1, 2):
+            w = workloads.advection1d(seed=seed, n=256, tiles=tiles)
+            W, _, _ = gpu_run(kin, w, w.steps)
+            _, Wo = oracle_run(w, w.steps)
+            l2, linf = rel_errors(w, W, Wo)
+            assert l2 < TOL64 and linf < TOL64, (tiles, seed, l2, linf)
+
+
+def test_vortex_2d_reduced_config_fp32_200_steps(kin):
+    # same subdomain geometry as the full 256^2 workload (32^2 cells per subdomain)
+    w = workloads.vortex2d(seed=0, n=64, degree=2, tiles=2)
+    w = workloads.with_(w, tiles=(2, 2))
+    W, _, _ = gpu_run(kin, w, 200)
+    _, Wo = oracle_run(w, 200)
+    l2, linf = rel_errors(w, W, Wo)
+    assert l2 < TOL32 and linf < TOL32, (l2, linf)
+
+
+def test_vortex_2d_full_config_fp32(kin):
+    # the benchmarked workload at full size: 256^2 cells, p = 2, 8x8 subdomains
+    w = workloads.vortex2d(seed=0)
+    w = workloads.with_(w, tiles=(8, 8))
+    steps = 3
+    W, _, info = gpu_run(kin, w, steps)
+    _, Wo = oracle_run(w, steps)
+    l2, linf = rel_errors(w, W, Wo)
+    assert l2 < TOL32 and linf < TOL32, (l2, linf)
+
+
+def test_density_wave_3d_reduced_config_fp32(kin):
+    # 32^3 cells with the full workload's 8^3-cell subdomains
+    w = workloads.densitywave3d(seed=0, n=32, degree=1, tiles=4)
+    w = workloads.with_(w, tiles=(4, 4, 4))
+    steps = 4
+    W, _, _ = gpu_run(kin, w, steps)
+    _, Wo = oracle_run(w, steps)
+    l2, linf = rel_errors(w, W, Wo)
+    assert l2 < TOL32 and linf < TOL32, (l2, linf)
+
+
+def test_block_shape_does_not_change_result(kin):
+    w = workloads.vortex2d(seed=6, n=32, degree=2, tiles=2, dt_mult=40.0, precision="f64")
+    w = workloads.with_(w, tiles=(2, 2))
+    ref = None
+    for block in [(8, 16), (4, 8), (2, 16), (1, 1)]:
+        W, _, _ = gpu_run(kin, w, 4, block=block)
+        if ref is None:
+            ref = W
+        else:
+            assert np.abs(W - ref).max() / np.abs(ref).max() < 1e-13
+
+
+def test_repeatable_bitwise_and_resume(kin):
+    w = workloads.vortex2d(seed=7, n=64, degree=2, tiles=2)
+    w = workloads.with_(w, tiles=(2, 2))
+    _, fa, _ = gpu_run(kin, w, 6)
+    _, fb, _ = gpu_run(kin, w, 6)
+    assert np.array_equal(fa, fb)
+    with kin.Context.from_workload(w) as c1:
+        c1.set_state(w.W0.reshape(-1).copy())
+        c1.step(3)
+        ck = c1.get_kinetic()
+    with kin.Context.from_workload(w) as c2:
+        c2.set_kinetic(ck)
+        c2.step(3)
+        fc = c2.get_kinetic()
+    assert np.array_equal(fa, fc)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mass_change_equals_interface_defect(kin, prec):
+    # Conservation: the only mass change of a step is the interface defect of
+    # the finite subdomain iteration (zero for a converged iteration); the
+    # GPU predicts it from its block summaries and it matches the oracle's.
+    w = workloads.vortex2d(seed=8, n=16, degree=2, tiles=2, dt_mult=40.0, precision=prec)
+    w = workloads.with_(w, tiles=(4, 4), iters=2)
+    P = oracle.Problem(**w.oracle_kwargs())
+    fo = oracle.init(P, w.W0)
+    with kin.Context.from_workload(w, block=(2, 2)) as ctx:
+        ctx.set_state(w.W0.reshape(-1).copy())
+        for _ in range(3):
+            m0, defect, resid = ctx.diag()
+            ctx.step(1)
+            m1, _, _ = ctx.diag()
+            d_or, _ = oracle.transport(P, fo)
+            oracle.relax(P, fo)
+            scale = np.abs(m0).max()
+            tol = (1e-13 if prec == "f64" else 1e-6) * scale
+            assert np.abs((m1 - m0) - defect).max() < tol
+            assert np.abs(defect - d_or).max() < tol
+            assert resid > 0 and np.abs(defect).max() > 1e-7
+
+
+def test_constant_state_preserved(kin):
+    w = workloads.densitywave3d(seed=0, n=16, degree=1, tiles=2)
+    W0 = w.W0.copy()
+    W0[0] = 1.0
+    W0[1:4] = 0.5
+    W0[4] = 3.0
+    w = workloads.with_(w, W0=W0, tiles=(2, 2, 2))
+    for prec in (kin.KIN_FP64, kin.KIN_FP32):
+        W, _, _ = gpu_run(kin, w, 5, precision=prec)
+        tol = 1e-14 if prec == kin.KIN_FP64 else 1e-6
+        assert np.abs(W - W0.reshape(-1)).max() < tol
+
+
+def test_runtime_errors_are_reported(kin):
+    w = workloads.advection1d(seed=0, n=16, tiles=2)
+    ctx = kin.Context.from_workload(w)
+    with pytest.raises(kin.KinError) as ei:
+        ctx.step(1)                               # no state yet
+    assert ei.value.status == kin.KIN_ESTATE
+    with pytest.raises(kin.KinError) as ei:
+        ctx.set_state(np.zeros(5))                # wrong size
+    assert ei.value.status == kin.KIN_EINVAL
+    with pytest.raises(kin.KinError) as ei:
+        kin.kin_step(ctx.ctx, -1)
+    assert ei.value.status == kin.KIN_EINVAL
+    ctx.close()
+    # memory budget
+    mesh, model, opts = kin.make_args(2, (64, 64), (0, 0), (1, 1), kin.KIN_EULER, 5.0,
+                                      tiles=(2, 2), precision=kin.KIN_FP32, mem_budget=1 << 16)
+    with pytest.raises(kin.KinError) as ei:
+        kin.kin_create(mesh, model, 2, 0.01, opts)
+    assert ei.value.status == kin.KIN_EBUDGET
+
+
+def test_torch_allocator_and_device_buffers(kin):
+    import torch
+    w = workloads.vortex2d(seed=9, n=32, degree=2, tiles=2)
+    w = workloads.with_(w, tiles=(2, 2))
+    stream = torch.cuda.Stream()
+    before = torch.cuda.memory_allocated()
+    ctx = kin.Context.from_workload(w, torch_alloc=True, stream=stream.cuda_stream)
+    assert torch.cuda.memory_allocated() - before >= ctx.info.device_bytes
+    Wd = torch.from_numpy(w.W0.reshape(-1).copy()).cuda()
+    torch.cuda.synchronize()
+    kin.kin_set_state(ctx.ctx, Wd)
+    ctx.step(2)
+    out = torch.empty_like(Wd)
+    kin.kin_get_state(ctx.ctx, out)
+    ctx.sync()
+    W_host, _, _ = gpu_run(kin, w, 2)
+    assert np.array_equal(out.cpu().numpy(), W_host)
+    ctx.close()

@@ -111,6 +111,10 @@ def node_coords(dim, n, lo, hi, degree) -> np.ndarray:
     return np.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], axis=1)
 
 
+def _tiles(tiles, dim):
+    return tuple(tiles) if isinstance(tiles, (tuple, list)) else (int(tiles),) * dim
+
+
 def _euler_conserved(rho, vel, pr, gamma):
     d = len(vel)
     E = pr / (gamma - 1.0) + 0.5 * rho * sum(u * u for u in vel)
@@ -140,7 +144,8 @@ def advection1d(seed: int = 0, n: int = 256, tiles: int = 1, iters: int = 3,
         return u0((x - a * t) % 1.0)[None, :]
 
     return Workload("advection1d", 1, (n,), (0.0,), (1.0,), degree, ADVECTION, lam, dt, omega, 1.4,
-                    (a, 0.0, 0.0), (tiles,), iters, steps, precision, u0(x)[None, :].copy(), exact)
+                    (a, 0.0, 0.0), _tiles(tiles, 1), iters, steps, precision,
+                    u0(x)[None, :].copy(), exact)
 
 
 def _vortex_fields(X, Y, xc, yc, eps, gamma, box, uinf, vinf):
@@ -180,7 +185,7 @@ def vortex2d(seed: int = 0, n: int = 256, degree: int = 2, tiles: int = 8, iters
 
     W0 = _euler_conserved(rho, vel, pr, gamma)
     return Workload("vortex2d", 2, (n, n), (0.0, 0.0), (box, box), degree, EULER, lam, dt, omega,
-                    gamma, (0.0, 0.0, 0.0), (tiles, tiles), iters, steps, precision, W0, exact)
+                    gamma, (0.0, 0.0, 0.0), _tiles(tiles, 2), iters, steps, precision, W0, exact)
 
 
 def _densitywave(dim, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision, amp=0.2):
@@ -209,7 +214,7 @@ def _densitywave(dim, seed, n, degree, tiles, iters, dt_mult, omega, steps, prec
         return _euler_conserved(r, vv, p, gamma)
 
     return Workload(f"densitywave{dim}d", dim, (n,) * dim, lo, hi, degree, EULER, lam, dt, omega,
-                    gamma, (0.0, 0.0, 0.0), (tiles,) * dim, iters, steps, precision,
+                    gamma, (0.0, 0.0, 0.0), _tiles(tiles, dim), iters, steps, precision,
                     _euler_conserved(rho, vel, pr, gamma), exact)
 
 
