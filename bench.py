@@ -77,17 +77,24 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0:    # wait until sampling is live
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+        self.window = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, t_begin, t_end):
+        self.window = (t_begin, t_end)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -99,19 +106,27 @@ class ClockSampler:
             self.thread.join(timeout=2)
 
     def summary(self):
-        if not self.rows:
+        rows = self.rows
+        if self.window is not None:
+            a, b = self.window
+            inside = [r for t, r in rows if a <= t <= b + 0.06]
+            rows = inside
+        else:
+            rows = [r for _, r in rows]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        self_rows = rows
+        sm = [float(r[1]) for r in self_rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for _, r in self.rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in self_rows:
             for i, nm in enumerate(names):
                 if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": sorted(reasons), "samples": len(self_rows)}
 
 
 def measured_peak_hbm():
@@ -140,21 +155,48 @@ def cpu_oracle_rate(w, budget_s=12.0, max_steps=50):
     return w.kinetic_dofs * steps / dt, steps, dt
 
 
+def reference_sample(w, name, steps, warmup, budget_s=100.0):
+    """A bounded sample of the workload for the oracle arm: the same problem
+    (same degree, velocity set, subdomain extent, time step and initial-data
+    recipe) on a mesh small enough that warmup + steps oracle steps fit the
+    time budget.  The oracle's cost per kinetic DOF does not depend on the
+    mesh size, so the DOF-update rate of the sample is that of the workload."""
+    import oracle
+    import workloads
+    if name != "vortex2d":
+        return w, "full workload"
+    sub = w.n[0] // w.tiles[0]               # subdomain extent (32 cells)
+    probe = workloads.vortex2d(seed=0, n=sub, tiles=1)
+    P = oracle.Problem(**probe.oracle_kwargs())
+    f = oracle.init(P, probe.W0)
+    t0 = time.perf_counter()
+    oracle.step(P, f, 2)
+    per_dof = (time.perf_counter() - t0) / (2 * probe.kinetic_dofs)
+    n = w.n[0]
+    while n > sub and per_dof * (steps + warmup) * (w.kinetic_dofs * (n / w.n[0]) ** 2) > budget_s:
+        n //= 2
+    if n == w.n[0]:
+        return w, "full workload"
+    s = workloads.vortex2d(seed=0, n=n, tiles=n // sub)
+    return s, f"{n}x{n} cells of the same recipe ({n // sub}x{n // sub} subdomains of {sub}^2 cells)"
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     w, desc = make_workload(args.workload)
     import oracle
-    P = oracle.Problem(**w.oracle_kwargs())
-    f = oracle.init(P, w.W0)
+    s, sample = reference_sample(w, args.workload, args.steps, args.warmup)
+    P = oracle.Problem(**s.oracle_kwargs())
+    f = oracle.init(P, s.W0)
     for _ in range(args.warmup):
         oracle.step(P, f, 1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.step(P, f, 1)
     el = time.perf_counter() - t0
-    value = w.kinetic_dofs * args.steps / el
+    value = s.kinetic_dofs * args.steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -162,7 +204,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": desc, "kinetic_dofs": w.kinetic_dofs, "parallelism": "cpu-1thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full steps of {desc} (after {args.warmup} warm-up)"},
+                         "sample": f"each step: one full step of {sample}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -297,7 +339,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="vortex2d",
