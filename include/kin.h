@@ -164,6 +164,36 @@ kin_status kin_get_kinetic(kin_ctx* ctx, void* f, size_t n_values, int on_device
  * |trace^{K} - trace^{K-1}|. */
 kin_status kin_diag(kin_ctx* ctx, double* mass_per_var, double* next_defect, double* iter_residual);
 
+/* kin_step_noalloc -- nsteps steps of S(dt) without any device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library allocate device memory -- host applications whose own
+ * memory pool reserves the device memory up front, and code that runs on a
+ * fixed memory plan where an allocation failure at run time is not
+ * acceptable.
+ *
+ * mesh, model, degree, dt: as kin_create.  opts: tiles, iters, precision,
+ * block and stream are used; mem_budget and the allocator hooks are ignored.
+ * f: device pointer to the caller's kinetic state, npop * nodes values of
+ * opts->precision in the storage order above; read as f^n and overwritten
+ * in place with f^{n + nsteps} (the caller owns it).  errbuf/errlen: optional
+ * buffer that receives a message on failure.
+ *
+ * Everything else the step needs (block-inverse coefficients, the
+ * Gauss-Lobatto rule, the block summaries) lives in one static device array
+ * of 16 MiB that every GPU loading this library holds until process exit.
+ * Problems whose scratch would exceed it are rejected with KIN_EINVAL and a
+ * message naming the limit; nothing is launched then.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call re-initialises the parts of the array it reads, so the previous
+ * call's leftovers never matter -- but all calls on a device share the one
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and corrupt each other: serialise them.
+ * Work is enqueued on opts->stream and the call returns without waiting;
+ * launch errors return KIN_ECUDA. */
+kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int degree, double dt,
+                            const kin_opts* opts, void* f, int nsteps, char* errbuf, size_t errlen);
+
 /* Block the host until the context's queued work is done. */
 kin_status kin_sync(kin_ctx* ctx);
 

@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
                 4: "KIN_ECUDA", 5: "KIN_ETIMEOUT", 6: "KIN_ESTATE"}
 
 EXPORTED = ["kin_create", "kin_set_state", "kin_set_kinetic", "kin_step", "kin_get_state",
-            "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error"]
+            "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error",
+            "kin_step_noalloc"]
 
 
 class KinError(RuntimeError):
@@ -96,6 +97,9 @@ def load_library():
     lib.kin_sync.argtypes = [vp]
     lib.kin_query.argtypes = [vp, ctypes.POINTER(kin_info)]
     lib.kin_destroy.argtypes = [vp]
+    lib.kin_step_noalloc.argtypes = [ctypes.POINTER(kin_mesh), ctypes.POINTER(kin_model), ctypes.c_int,
+                                     ctypes.c_double, ctypes.POINTER(kin_opts), vp, ctypes.c_int,
+                                     ctypes.c_char_p, sz]
     lib.kin_last_error.argtypes = [vp]
     lib.kin_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -207,6 +211,23 @@ def kin_query(ctx) -> kin_info:
 
 def kin_destroy(ctx):
     _check(None, load_library().kin_destroy(ctx))
+
+
+def kin_step_noalloc(mesh: kin_mesh, model: kin_model, degree: int, dt: float, opts: kin_opts,
+                     f, nsteps: int):
+    """Advance the caller's device kinetic state f (a CUDA tensor, updated in
+    place) by nsteps steps without any device allocation by the library; its
+    scratch is a static 16 MiB device array shared by all calls on a device,
+    so calls must not overlap on the GPU.  For callers whose device memory is
+    owned by their own allocator or fixed memory plan."""
+    p, dev = _ptr(f)
+    if not dev:
+        raise ValueError("kin_step_noalloc needs a device buffer")
+    err = ctypes.create_string_buffer(512)
+    st = load_library().kin_step_noalloc(ctypes.byref(mesh), ctypes.byref(model), degree, dt,
+                                         ctypes.byref(opts), p, nsteps, err, len(err))
+    if st != KIN_OK:
+        raise KinError(st, err.value.decode())
 
 
 def kin_last_error(ctx=None) -> str:

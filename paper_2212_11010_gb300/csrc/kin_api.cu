@@ -588,3 +588,230 @@ const char* kin_last_error(const kin_ctx* c)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// kin_step_noalloc: the step kernels with their scratch in a static device
+// array, for callers that cannot allocate device memory.
+//
+// Some callers cannot let a library call cudaMalloc: host applications whose
+// own memory pool reserves the device's memory up front (a library
+// allocation would fail or fragment that pool), and code paths that run on a
+// fixed memory plan where an allocation failure at run time is not
+// acceptable.  This entry point takes the caller's kinetic state and keeps
+// everything else it needs -- the FP64/FP32 block-inverse coefficients, the
+// Gauss-Lobatto rule and the two ping-pong copies of the block summaries --
+// in g_noalloc_scratch below.
+//
+// The array is a file-scope __device__ object, so every GPU that loads this
+// library holds kNoallocScratchBytes of it until the process exits.  Host
+// code may not use its name as an address: the address is taken once per
+// device, with that device current, by cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = size_t(16) << 20;   // 16 MiB per device
+constexpr int kNoallocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+void noalloc_msg(char* buf, size_t len, const char* fmt, ...)
+{
+    if (!buf || !len) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, len, fmt, ap);
+    va_end(ap);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int degree,
+                                       double dt, const kin_opts* opts, void* f, int nsteps,
+                                       char* errbuf, size_t errlen)
+{
+    if (errbuf && errlen) errbuf[0] = '\0';
+    if (!mesh || !model || !opts || !f) {
+        noalloc_msg(errbuf, errlen, "mesh, model, opts and f are required");
+        return KIN_EINVAL;
+    }
+    if (nsteps < 0) {
+        noalloc_msg(errbuf, errlen, "nsteps must be >= 0");
+        return KIN_EINVAL;
+    }
+    if (mesh->dim < 1 || mesh->dim > 3 || degree < 1 || degree > 3 ||
+        (model->system != KIN_ADVECTION && model->system != KIN_EULER) || model->velset != mesh->dim ||
+        !(model->lambda > 0) || !(dt > 0) || !(model->omega >= 1.0 && model->omega <= 2.0) ||
+        (model->system == KIN_EULER && !(model->gamma > 1.0)) || opts->iters < 1 ||
+        (opts->precision != KIN_FP64 && opts->precision != KIN_FP32)) {
+        noalloc_msg(errbuf, errlen, "invalid mesh, model, degree, dt or opts (same rules as kin_create)");
+        return KIN_EINVAL;
+    }
+
+    // The same problem set-up as kin_create, on the stack: the buffers point
+    // into the static scratch instead of allocations.
+    kin_ctx c;
+    c.dim = mesh->dim;
+    c.degree = degree;
+    c.system = model->system;
+    c.m = model->system == KIN_EULER ? mesh->dim + 2 : 1;
+    c.nvel = 2 * mesh->dim;
+    c.npop = c.nvel * c.m;
+    c.NP = degree + 1;
+    c.NN = 1;
+    for (int a = 0; a < c.dim; ++a) c.NN *= c.NP;
+    c.lambda = model->lambda;
+    c.gamma = model->gamma;
+    c.omega = model->omega;
+    c.dt = dt;
+    c.iters = opts->iters;
+    c.precision = opts->precision;
+    c.esize = opts->precision == KIN_FP32 ? 4 : 8;
+    c.stream = (cudaStream_t)opts->stream;
+    c.cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        c.adv[a] = model->adv[a];
+        if (a < c.dim) {
+            if (mesh->n[a] < 1 || !(mesh->hi[a] > mesh->lo[a]) || opts->tiles[a] < 1 ||
+                mesh->n[a] % opts->tiles[a]) {
+                noalloc_msg(errbuf, errlen, "axis %d: need n >= 1, hi > lo and tiles dividing n", a);
+                return KIN_EINVAL;
+            }
+            c.n[a] = mesh->n[a];
+            c.lo[a] = mesh->lo[a];
+            c.hi[a] = mesh->hi[a];
+            c.h[a] = (mesh->hi[a] - mesh->lo[a]) / mesh->n[a];
+            c.tiles[a] = opts->tiles[a];
+            c.L[a] = c.n[a] / c.tiles[a];
+        } else {
+            if (mesh->n[a] > 1) {
+                noalloc_msg(errbuf, errlen, "axis %d beyond dim must have n = 1", a);
+                return KIN_EINVAL;
+            }
+            c.n[a] = 1;
+            c.tiles[a] = 1;
+            c.L[a] = 1;
+        }
+        c.cells *= c.n[a];
+    }
+    c.nodes = c.cells * c.NN;
+    if (opts->block[0] || opts->block[1] || opts->block[2]) {
+        for (int a = 0; a < 3; ++a) {
+            int b = a < c.dim ? opts->block[a] : 1;
+            if (b < 1 || c.L[a] % b) {
+                noalloc_msg(errbuf, errlen, "axis %d: block %d must divide the subdomain extent %d", a, b, c.L[a]);
+                return KIN_EINVAL;
+            }
+            c.B[a] = b;
+        }
+    } else {
+        choose_block(&c, c.B);
+    }
+    for (int a = 0; a < 3; ++a) {
+        c.nblk[a] = c.n[a] / c.B[a];
+        c.nb[a] = c.L[a] / c.B[a];
+    }
+    const size_t smem = block_smem(&c, c.B);
+    if (smem > 227 * 1024) {
+        noalloc_msg(errbuf, errlen, "cell block needs %zu bytes of shared memory (> 227 KB)", smem);
+        return KIN_EINVAL;
+    }
+    c.smem = (int)smem;
+    c.grid = c.nblk[0] * c.nblk[1] * c.nblk[2];
+    c.kfn = pick_kernel(c.dim, degree, c.system, c.precision);
+    size_t tn = 1;
+    for (int a = 1; a < c.dim; ++a) tn *= c.NP;
+    size_t stride = 0;
+    for (int a = 0; a < c.dim; ++a)
+        stride = std::max(stride, (size_t)c.nblk[a] * (c.cells / c.n[a]) * tn);
+    c.sig_stride = stride;
+
+    // scratch layout: c64 | c32 | gll | sig0 | raw0 | sig1 | raw1
+    const size_t off_c64 = 0;
+    const size_t off_c32 = align256(off_c64 + sizeof(double) * 6 * kCoefStride);
+    const size_t off_gll = align256(off_c32 + sizeof(float) * 6 * kCoefStride);
+    const size_t off_sum = align256(off_gll + sizeof(double) * 2 * kMaxNP);
+    const size_t sbytes = align256(stride * c.npop * c.esize);
+    const size_t need = off_sum + 4 * sbytes;
+    if (need > kNoallocScratchBytes) {
+        noalloc_msg(errbuf, errlen,
+                    "problem needs %zu bytes of scratch; kin_step_noalloc is limited to %zu bytes "
+                    "(use kin_create for larger problems)", need, kNoallocScratchBytes);
+        return KIN_EINVAL;
+    }
+
+    // per-device address of the static scratch (first call on each device)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        noalloc_msg(errbuf, errlen, "cudaGetDevice failed or device ordinal out of range");
+        return KIN_ECUDA;
+    }
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                noalloc_msg(errbuf, errlen, "cudaGetSymbolAddress(g_noalloc_scratch) failed: %s",
+                            cudaGetErrorString(e));
+                return KIN_ECUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    }
+    c.f = f;
+    c.c64 = reinterpret_cast<double*>(base + off_c64);
+    c.coef = c.esize == 4 ? (void*)(base + off_c32) : (void*)c.c64;
+    c.gll = reinterpret_cast<double*>(base + off_gll);
+    c.sig[0] = base + off_sum;
+    c.raw[0] = base + off_sum + sbytes;
+    c.sig[1] = base + off_sum + 2 * sbytes;
+    c.raw[1] = base + off_sum + 3 * sbytes;
+    c.cur = 0;
+
+    if (c.smem > 48 * 1024) {
+        e = cudaFuncSetAttribute((const void*)c.kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
+        if (e != cudaSuccess) {
+            noalloc_msg(errbuf, errlen, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
+            return KIN_ECUDA;
+        }
+    }
+    SetupArgs sa;
+    memset(&sa, 0, sizeof sa);
+    sa.dim = c.dim;
+    sa.degree = degree;
+    sa.lambda = c.lambda;
+    sa.dt = dt;
+    for (int a = 0; a < 3; ++a) {
+        sa.h[a] = c.h[a];
+        sa.B[a] = c.B[a];
+    }
+    sa.c64 = c.c64;
+    sa.c32 = c.esize == 4 ? (float*)c.coef : nullptr;
+    sa.gll = c.gll;
+    e = launch_setup(sa, c.stream);
+    // summaries of the caller's state, then nsteps full steps (every scratch
+    // region is written before it is read, so nothing needs clearing)
+    for (int s = 0; e == cudaSuccess && s <= nsteps; ++s) {
+        Inst I = make_inst(&c, s == 0 ? 1 : 0);
+        void* args[] = {&I};
+        e = cudaLaunchKernel((const void*)c.kfn, dim3(c.grid), dim3(kThreads), args, (size_t)c.smem,
+                             c.stream);
+        c.cur ^= 1;
+    }
+    if (e != cudaSuccess) {
+        noalloc_msg(errbuf, errlen, "kernel launch failed: %s", cudaGetErrorString(e));
+        return KIN_ECUDA;
+    }
+    return KIN_OK;
+}
