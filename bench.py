@@ -35,6 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "kinetic-DOF updates/s"
 UNIT = "DOF-updates/s"
 ALGO_BYTES_PER_DOF = {"f32": 8, "f64": 16}   # read f^n once + write f^{n+1} once
+# DRAM bytes (read + write) of one step launch from an ncu capture of the same
+# kernel and workload (profiles/step_kernel_fixed_vortex2d_256x256_p2.md);
+# stores still in L2 at kernel end are not counted by the capture.
+NCU_TRAFFIC = {("vortex2d", "f32"): 39.769600e6 + 0.047104e6}
 
 
 def make_workload(name):
@@ -317,7 +321,7 @@ def run_ours(args):
                        "smem_bytes": ctx.info.smem_bytes,
                        "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, prec)),
                          "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes},
             "e2e": {"value": dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": fbytes,
                     "d2h_bytes_per_step": fbytes},

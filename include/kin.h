@@ -104,7 +104,17 @@ typedef struct {
     kin_alloc_fn alloc;
     kin_free_fn free;
     void* alloc_user;
+    double wait_timeout_s;  /* bound on every device-side wait (0 = 1 s)        */
+    int debug_flags;        /* KIN_DEBUG_* test hooks; 0 in production          */
+    int threads;            /* threads per thread block, 32..256 (0 = auto)     */
+    int stages;             /* shared-memory tile buffers, 1 or 2 (0 = auto)    */
 } kin_opts;
+
+/* Test hook: the bulk-load barrier of every thread block expects 16 bytes
+ * that never arrive, so its bounded wait runs out; the step reports
+ * KIN_ETIMEOUT at the next synchronising call and the CUDA context stays
+ * usable. */
+enum { KIN_DEBUG_STALL_LOAD = 1 };
 
 /* Sizes of a context. */
 typedef struct {
@@ -117,7 +127,10 @@ typedef struct {
     int block[3];                   /* thread-block cell extents in use        */
     int smem_bytes;                 /* dynamic shared memory per thread block  */
     int grid;                       /* thread blocks per step launch           */
+    int threads;                    /* threads per thread block                */
+    int stages;                     /* shared-memory tile buffers              */
     long long steps_done;
+    int specialised;                /* 1: compile-time block-shape kernel      */
 } kin_info;
 
 /* Create a context: validates arguments, computes on the GPU in FP64 the
@@ -189,8 +202,8 @@ kin_status kin_diag(kin_ctx* ctx, double* mass_per_var, double* next_defect, dou
  * call's leftovers never matter -- but all calls on a device share the one
  * array, so calls whose work overlaps on the GPU (different streams, or
  * different host threads) race and corrupt each other: serialise them.
- * Work is enqueued on opts->stream and the call returns without waiting;
- * launch errors return KIN_ECUDA. */
+ * Work runs on opts->stream; the call returns once that stream has drained
+ * (KIN_ECUDA on a CUDA error, KIN_ETIMEOUT if a bounded device wait ran out). */
 kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int degree, double dt,
                             const kin_opts* opts, void* f, int nsteps, char* errbuf, size_t errlen);
 

@@ -25,6 +25,7 @@ KIN_OK, KIN_EINVAL, KIN_ENOMEM, KIN_EBUDGET, KIN_ECUDA, KIN_ETIMEOUT, KIN_ESTATE
 KIN_ADVECTION, KIN_EULER = 0, 1
 KIN_D1Q2, KIN_D2Q4, KIN_D3Q6 = 1, 2, 3
 KIN_FP64, KIN_FP32 = 0, 1
+KIN_DEBUG_STALL_LOAD = 1
 
 STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
                 4: "KIN_ECUDA", 5: "KIN_ETIMEOUT", 6: "KIN_ESTATE"}
@@ -58,7 +59,8 @@ class kin_opts(ctypes.Structure):
     _fields_ = [("tiles", ctypes.c_int * 3), ("iters", ctypes.c_int), ("precision", ctypes.c_int),
                 ("block", ctypes.c_int * 3), ("mem_budget", ctypes.c_size_t),
                 ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p)]
+                ("alloc_user", ctypes.c_void_p), ("wait_timeout_s", ctypes.c_double),
+                ("debug_flags", ctypes.c_int), ("threads", ctypes.c_int), ("stages", ctypes.c_int)]
 
 
 class kin_info(ctypes.Structure):
@@ -68,7 +70,8 @@ class kin_info(ctypes.Structure):
                 ("kinetic_values", ctypes.c_size_t), ("state_values", ctypes.c_size_t),
                 ("device_bytes", ctypes.c_size_t), ("precision", ctypes.c_int),
                 ("block", ctypes.c_int * 3), ("smem_bytes", ctypes.c_int), ("grid", ctypes.c_int),
-                ("steps_done", ctypes.c_longlong)]
+                ("threads", ctypes.c_int), ("stages", ctypes.c_int), ("steps_done", ctypes.c_longlong),
+                ("specialised", ctypes.c_int)]
 
 
 _lib = None
@@ -240,7 +243,7 @@ def kin_last_error(ctx=None) -> str:
 
 def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 0.0),
               tiles=(1, 1, 1), iters=3, precision=KIN_FP64, block=(0, 0, 0), mem_budget=0,
-              stream=None, torch_alloc=False):
+              stream=None, torch_alloc=False, wait_timeout_s=0.0, debug_flags=0, threads=0, stages=0):
     pad = lambda t, fill: tuple(t) + (fill,) * (3 - len(tuple(t)))
     mesh = kin_mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
                     (ctypes.c_double * 3)(*pad(hi, 1.0)))
@@ -252,6 +255,10 @@ def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 
     opts.block = (ctypes.c_int * 3)(*pad(block, 0))
     opts.mem_budget = mem_budget
     opts.stream = stream
+    opts.wait_timeout_s = wait_timeout_s
+    opts.debug_flags = debug_flags
+    opts.threads = threads
+    opts.stages = stages
     if torch_alloc:
         a, f = torch_allocator_hooks()
         opts.alloc = a

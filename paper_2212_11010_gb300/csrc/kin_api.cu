@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -23,7 +24,8 @@ struct kin_ctx {
     double lambda = 1, gamma = 1.4, adv[3] = {0, 0, 0}, omega = 2, dt = 0;
     int tiles[3] = {1, 1, 1}, L[3] = {1, 1, 1}, iters = 3, precision = KIN_FP64;
     int B[3] = {1, 1, 1}, nblk[3] = {1, 1, 1}, nb[3] = {1, 1, 1};
-    size_t cells = 0, nodes = 0, sig_stride = 0, esize = 8;
+    size_t cells = 0, nodes = 0, sig_stride = 0, raw_stride = 0, esize = 8;
+    double coef_host[6][kCoefStride] = {};   // FP64 block-inverse records (device-computed)
     // runtime
     cudaStream_t stream = nullptr;
     kin_alloc_fn alloc = nullptr;
@@ -41,8 +43,13 @@ struct kin_ctx {
     double* Wbuf = nullptr;
     double* partial = nullptr;
     double* result = nullptr;
+    int* errword = nullptr;
+    double wait_timeout_s = 1.0;
+    int debug_flags = 0;
     StepKernel kfn = nullptr;
-    int smem = 0, grid = 0;
+    int smem = 0, grid = 0, stages = 1, threads = kThreads;
+    int want_threads = 0, want_stages = 0;
+    bool fixed = false;                    // compile-time block shape kernel in use
     bool have_state = false;
     long long steps_done = 0;
     bool poisoned = false;
@@ -133,11 +140,27 @@ static int next_divisor_below(int L, int b)
 }
 
 // Default cell block: start from the whole subdomain and shrink the longest
-// extent until the block fits the shared-memory target and the grid has
-// enough blocks to fill 152 SMs twice.
+// extent (z before y before x on ties, to keep the contiguous x rows long)
+// until one tile fits the shared-memory target -- two tiles then fit twice
+// per SM -- and the grid has enough tiles to fill 152 SMs twice.
 static void choose_block(const kin_ctx* c, int B[3])
 {
-    const size_t target = 64 * 1024;
+    // a block shape with a compiled fixed-shape kernel, if one fits the subdomains
+    int shapes[4][3];
+    const int ns = fixed_shapes(c->dim, c->degree, c->system, c->precision, shapes);
+    for (int k = 0; k < ns; ++k) {
+        bool fits = true;
+        long long tiles = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (c->L[a] % shapes[k][a]) fits = false;
+            tiles *= c->n[a] / shapes[k][a];
+        }
+        if (fits && tiles >= 152) {
+            for (int a = 0; a < 3; ++a) B[a] = shapes[k][a];
+            return;
+        }
+    }
+    const size_t target = 48 * 1024;
     for (int a = 0; a < 3; ++a) B[a] = c->L[a];
     auto grid_of = [&](const int* b) {
         long long g = 1;
@@ -149,12 +172,22 @@ static void choose_block(const kin_ctx* c, int B[3])
         bool too_few = grid_of(B) < 2 * 152;
         if (!too_big && !too_few) break;
         int best = -1;
-        for (int a = 0; a < c->dim; ++a)
+        for (int a = c->dim - 1; a >= 0; --a)
             if (B[a] > 1 && (best < 0 || B[a] > B[best])) best = a;
         if (best < 0) break;
         if (!too_big && B[best] <= 4) break;     // keep lines reasonably long
         B[best] = next_divisor_below(c->L[best], B[best]);
     }
+}
+
+// Bulk copies need every row of a cell block to start on a 16-byte
+// boundary and to span a multiple of 16 bytes.
+static bool rows_are_16b_aligned(const kin_ctx* c)
+{
+    const size_t rowb = (size_t)c->B[0] * c->NN * c->esize;
+    const size_t popb = c->nodes * c->esize;
+    const size_t lineb = (size_t)c->n[0] * c->NN * c->esize;
+    return rowb % 16 == 0 && popb % 16 == 0 && lineb % 16 == 0 && ((uintptr_t)c->f % 16) == 0;
 }
 
 static Inst make_inst(const kin_ctx* c, int mode)
@@ -166,9 +199,19 @@ static Inst make_inst(const kin_ctx* c, int mode)
     I.raw_in = c->raw[c->cur];
     I.sig_out = c->sig[c->cur ^ 1];
     I.raw_out = c->raw[c->cur ^ 1];
-    I.coef = c->coef;
+    I.err = c->errword;
     I.nodes = (long long)c->nodes;
     I.sig_stride = (long long)c->sig_stride;
+    I.raw_stride = (long long)c->raw_stride;
+    for (int d = 0; d < 6; ++d)
+        for (int k = 0; k < kCoefStride; ++k) {
+            I.cd[d][k] = c->coef_host[d][k];
+            I.cf[d][k] = (float)c->coef_host[d][k];
+        }
+    I.wait_cycles = (long long)((c->wait_timeout_s > 0 ? c->wait_timeout_s : 1.0) * 2.2e9);
+    long long tn = 1;
+    for (int a = 1; a < c->dim; ++a) tn *= c->NP;
+    const int bcells = c->B[0] * c->B[1] * c->B[2];
     for (int a = 0; a < 3; ++a) {
         I.n[a] = c->n[a];
         I.B[a] = c->B[a];
@@ -176,13 +219,110 @@ static Inst make_inst(const kin_ctx* c, int mode)
         I.nb[a] = c->nb[a];
         I.NS[a] = c->tiles[a];
         I.adv[a] = c->adv[a];
+        I.ax[a].lines = make_fastdiv((unsigned)((bcells / c->B[a]) * tn));
+        I.ax[a].e1 = make_fastdiv((unsigned)(a == 0 ? c->B[1] : c->B[0]));
+        I.ax[a].glines = (long long)(c->cells / c->n[a]) * tn;
     }
+    I.fd_nrows = make_fastdiv((unsigned)(c->B[1] * c->B[2]));
+    I.fd_B1 = make_fastdiv((unsigned)c->B[1]);
+    I.fd_rowlen = make_fastdiv((unsigned)(c->B[0] * c->NN));
     I.iters = c->iters;
     I.mode = mode;
+    I.tma = rows_are_16b_aligned(c) ? 1 : 0;
+    I.stages = c->stages;
+    I.debug_stall = (c->debug_flags & KIN_DEBUG_STALL_LOAD) ? 1 : 0;
     I.lambda = c->lambda;
     I.gamma = c->gamma;
     I.omega = c->omega;
     return I;
+}
+
+// Read the device error word (after the stream has been synchronised).
+static kin_status check_errword(kin_ctx* c)
+{
+    int h = 0;
+    KIN_CUDA(c, cudaMemcpyAsync(&h, c->errword, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h & kErrLoadTimeout)
+        return fail(c, KIN_ETIMEOUT, "a thread block gave up waiting for its bulk loads (bounded wait ran out)");
+    if (h) return fail(c, KIN_ETIMEOUT, "device error word 0x%x", h);
+    return KIN_OK;
+}
+
+// Work items of one tile: (population, line) pairs per axis and nodes.
+static void tile_work(const kin_ctx* c, long long items[3], long long* nodes)
+{
+    const long long bcells = (long long)c->B[0] * c->B[1] * c->B[2];
+    long long tn = 1;
+    for (int a = 1; a < c->dim; ++a) tn *= c->NP;
+    for (int a = 0; a < 3; ++a) items[a] = a < c->dim ? 2LL * c->m * (bcells / c->B[a]) * tn : 0;
+    *nodes = bcells * c->NN;
+}
+
+// Threads per block: the multiple of 32 in [128, 256] that leaves the fewest
+// idle thread-slots over the phases of a tile (per-axis line items twice --
+// transport and summaries -- and the relaxation nodes); ties go to more threads.
+static int choose_threads(const kin_ctx* c)
+{
+    long long items[3], nodes;
+    tile_work(c, items, &nodes);
+    int best = kThreads;
+    long long best_cost = -1;
+    for (int nth = kThreads; nth >= 128; nth -= 32) {
+        long long cost = ((nodes + nth - 1) / nth) * nth;
+        for (int a = 0; a < c->dim; ++a) cost += 2 * ((items[a] + nth - 1) / nth) * nth;
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = nth;
+        }
+    }
+    return best;
+}
+
+// Launch shape: threads, shared-memory stages (two when rows move by bulk
+// copies and two tiles fit), carve-out, resident blocks per SM and the
+// persistent grid.  Dynamic shared memory = stages x tile + inflow traces.
+static cudaError_t configure_launch(kin_ctx* c)
+{
+    const size_t tile = block_smem(c, c->B);
+    long long items[3], nodes;
+    tile_work(c, items, &nodes);
+    const size_t tin = ((size_t)(items[0] + items[1] + items[2]) * c->esize + 15) & ~size_t(15);
+    const bool tma = rows_are_16b_aligned(c);
+    // fixed-shape kernel: same result, compile-time shape (bulk copies, one stage)
+    FixedKernel fk{nullptr, 0, 0};
+    if (c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B);
+    if (c->dim == 3) fk = fixed_kernel_d3(c->degree, c->system, c->precision, c->B);
+    c->fixed = fk.fn && tma && (c->want_threads == 0 || c->want_threads == fk.threads) && c->want_stages != 2;
+    if (c->fixed) {
+        c->kfn = fk.fn;
+        c->threads = fk.threads;
+        c->stages = 1;
+        c->smem = (int)fk.smem;
+    } else {
+        c->kfn = pick_kernel(c->dim, c->degree, c->system, c->precision);
+        c->threads = c->want_threads ? c->want_threads : choose_threads(c);
+        if (!tma) c->stages = 1;
+        else if (c->want_stages) c->stages = c->want_stages;
+        else c->stages = 1;
+        if (c->stages * tile + tin > 227 * 1024) c->stages = 1;
+        c->smem = (int)(c->stages * tile + tin);
+    }
+    cudaError_t e = cudaSuccess;
+    if (c->smem > 48 * 1024)
+        e = cudaFuncSetAttribute((const void*)c->kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)c->kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int dev = 0, nsm = 1, occ = 1;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)c->kfn, c->threads, c->smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const long long ntiles = (long long)c->nblk[0] * c->nblk[1] * c->nblk[2];
+    c->grid = (int)std::min<long long>(ntiles, (long long)occ * nsm);
+    return cudaSuccess;
 }
 
 // Launch of the fused kernel: mode 0 = one full step, mode 1 = block
@@ -191,7 +331,7 @@ static kin_status launch_step(kin_ctx* c, int mode)
 {
     Inst I = make_inst(c, mode);
     void* args[] = {&I};
-    KIN_CUDA(c, cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(kThreads), args,
+    KIN_CUDA(c, cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(c->threads), args,
                                  (size_t)c->smem, c->stream));
     c->cur ^= 1;
     return KIN_OK;
@@ -248,6 +388,9 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
         return fail(nullptr, KIN_EINVAL, "unknown precision %d", opts->precision);
     if ((opts->alloc == nullptr) != (opts->free == nullptr))
         return fail(nullptr, KIN_EINVAL, "alloc and free hooks must be given together");
+    if (opts->threads != 0 && (opts->threads < 32 || opts->threads > kThreads || opts->threads % 32))
+        return fail(nullptr, KIN_EINVAL, "threads must be 0 or a multiple of 32 in [32, %d]", kThreads);
+    if (opts->stages < 0 || opts->stages > 2) return fail(nullptr, KIN_EINVAL, "stages must be 0, 1 or 2");
 
     kin_ctx* c = new (std::nothrow) kin_ctx();
     if (!c) return fail(nullptr, KIN_ENOMEM, "host allocation failed");
@@ -272,6 +415,10 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     c->dealloc = opts->free;
     c->alloc_user = opts->alloc_user;
     c->budget = opts->mem_budget;
+    c->wait_timeout_s = opts->wait_timeout_s;
+    c->debug_flags = opts->debug_flags;
+    c->want_threads = opts->threads;
+    c->want_stages = opts->stages;
     c->cells = 1;
     for (int a = 0; a < 3; ++a) {
         c->adv[a] = model->adv[a];
@@ -328,8 +475,6 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
         delete c;
         return fail(nullptr, KIN_EINVAL, "cell block needs %zu bytes of shared memory (> 227 KB)", smem);
     }
-    c->smem = (int)smem;
-    c->grid = c->nblk[0] * c->nblk[1] * c->nblk[2];
     c->kfn = pick_kernel(c->dim, degree, c->system, c->precision);
     if (!c->kfn) {
         delete c;
@@ -339,14 +484,18 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     // summaries: per population, n[a]/B[a] blocks x (cells / n[a]) x NP^{d-1} lines
     size_t tn = 1;
     for (int a = 1; a < c->dim; ++a) tn *= c->NP;
-    size_t stride = 0;
-    for (int a = 0; a < c->dim; ++a)
+    size_t stride = 0, rstride = 0;
+    for (int a = 0; a < c->dim; ++a) {
         stride = std::max(stride, (size_t)c->nblk[a] * (c->cells / c->n[a]) * tn);
+        rstride = std::max(rstride, (size_t)c->tiles[a] * (c->cells / c->n[a]) * tn);
+    }
     c->sig_stride = stride;
+    c->raw_stride = rstride;
 
     kin_status st;
     const size_t fbytes = c->nodes * c->npop * c->esize;
     const size_t sbytes = stride * c->npop * c->esize;
+    const size_t rbytes = rstride * c->npop * c->esize;
     void* p;
 #define ALLOC(dst, bytes)                                                 \
     do {                                                                  \
@@ -362,7 +511,7 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     ALLOC(c->f, fbytes);
     for (int i = 0; i < 2; ++i) {
         ALLOC(c->sig[i], sbytes);
-        ALLOC(c->raw[i], sbytes);
+        ALLOC(c->raw[i], rbytes);
     }
     ALLOC(c->c64, sizeof(double) * 6 * kCoefStride);
     ALLOC(c->coef, c->esize == 4 ? sizeof(float) * 6 * kCoefStride : 16);
@@ -370,14 +519,14 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     ALLOC(c->Wbuf, sizeof(double) * c->m * c->nodes);
     ALLOC(c->partial, sizeof(double) * kDiagBlocks * 6);
     ALLOC(c->result, sizeof(double) * 8);
+    ALLOC(c->errword, sizeof(int) * 4);
 #undef ALLOC
     if (c->esize == 8) c->coef = c->c64;
 
-    if (c->smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)c->kfn,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem);
+    {
+        cudaError_t e = configure_launch(c);
         if (e != cudaSuccess) {
-            g_create_error = std::string("cudaFuncSetAttribute failed: ") + cudaGetErrorString(e);
+            g_create_error = std::string("launch configuration failed: ") + cudaGetErrorString(e);
             release_all(c);
             delete c;
             return KIN_ECUDA;
@@ -397,7 +546,10 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     sa.c64 = c->c64;
     sa.c32 = c->esize == 4 ? (float*)c->coef : nullptr;
     sa.gll = c->gll;
-    cudaError_t e = launch_setup(sa, c->stream);
+    cudaError_t e = cudaMemsetAsync(c->errword, 0, sizeof(int) * 4, c->stream);
+    if (e == cudaSuccess) e = launch_setup(sa, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->coef_host, c->c64, sizeof(c->coef_host), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         g_create_error = std::string("setup kernel failed: ") + cudaGetErrorString(e);
@@ -425,9 +577,12 @@ kin_status kin_set_state(kin_ctx* c, const double* W, size_t n_values, int on_de
     KIN_CUDA(c, launch_init(point_args(c), src, c->f, c->precision == KIN_FP32, c->stream));
     st = launch_step(c, 1);
     if (st) return st;
-    if (!on_device) KIN_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_state = true;
     c->steps_done = 0;
+    if (!on_device) {
+        KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+        return check_errword(c);
+    }
     return KIN_OK;
 }
 
@@ -442,8 +597,11 @@ kin_status kin_set_kinetic(kin_ctx* c, const void* f, size_t n_values, int on_de
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     st = launch_step(c, 1);
     if (st) return st;
-    if (!on_device) KIN_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_state = true;
+    if (!on_device) {
+        KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+        return check_errword(c);
+    }
     return KIN_OK;
 }
 
@@ -475,6 +633,7 @@ kin_status kin_get_state(kin_ctx* c, double* W, size_t n_values, int on_device)
         KIN_CUDA(c, cudaMemcpyAsync(W, c->Wbuf, n_values * sizeof(double), cudaMemcpyDeviceToHost,
                                     c->stream));
         KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+        return check_errword(c);
     }
     return KIN_OK;
 }
@@ -489,7 +648,10 @@ kin_status kin_get_kinetic(kin_ctx* c, void* f, size_t n_values, int on_device)
     if (!c->have_state) return fail(c, KIN_ESTATE, "no state has been set");
     KIN_CUDA(c, cudaMemcpyAsync(f, c->f, n_values * c->esize,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-    if (!on_device) KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!on_device) {
+        KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+        return check_errword(c);
+    }
     return KIN_OK;
 }
 
@@ -514,6 +676,7 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
         da.m = c->m;
         da.iters = c->iters;
         da.sig_stride = (long long)c->sig_stride;
+        da.raw_stride = (long long)c->raw_stride;
         da.dt = c->dt;
         da.lambda = c->lambda;
         long long tn = 1;
@@ -538,7 +701,7 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
             for (int v = 0; v < c->m; ++v) next_defect[v] = host[v];
         if (iter_residual) *iter_residual = host[5];
     }
-    return KIN_OK;
+    return check_errword(c);
 }
 
 kin_status kin_sync(kin_ctx* c)
@@ -546,7 +709,7 @@ kin_status kin_sync(kin_ctx* c)
     kin_status st = check_usable(c);
     if (st) return st;
     KIN_CUDA(c, cudaStreamSynchronize(c->stream));
-    return KIN_OK;
+    return check_errword(c);
 }
 
 kin_status kin_query(const kin_ctx* c, kin_info* info)
@@ -568,6 +731,9 @@ kin_status kin_query(const kin_ctx* c, kin_info* info)
     for (int a = 0; a < 3; ++a) info->block[a] = c->B[a];
     info->smem_bytes = c->smem;
     info->grid = c->grid;
+    info->threads = c->threads;
+    info->stages = c->stages;
+    info->specialised = c->fixed ? 1 : 0;
     info->steps_done = c->steps_done;
     return KIN_OK;
 }
@@ -675,6 +841,16 @@ extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* mo
     c.precision = opts->precision;
     c.esize = opts->precision == KIN_FP32 ? 4 : 8;
     c.stream = (cudaStream_t)opts->stream;
+    if (opts->threads != 0 && (opts->threads < 32 || opts->threads > kThreads || opts->threads % 32)) {
+        noalloc_msg(errbuf, errlen, "threads must be 0 or a multiple of 32 in [32, %d]", kThreads);
+        return KIN_EINVAL;
+    }
+    if (opts->stages < 0 || opts->stages > 2) {
+        noalloc_msg(errbuf, errlen, "stages must be 0, 1 or 2");
+        return KIN_EINVAL;
+    }
+    c.want_threads = opts->threads;
+    c.want_stages = opts->stages;
     c.cells = 1;
     for (int a = 0; a < 3; ++a) {
         c.adv[a] = model->adv[a];
@@ -723,23 +899,26 @@ extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* mo
         noalloc_msg(errbuf, errlen, "cell block needs %zu bytes of shared memory (> 227 KB)", smem);
         return KIN_EINVAL;
     }
-    c.smem = (int)smem;
-    c.grid = c.nblk[0] * c.nblk[1] * c.nblk[2];
     c.kfn = pick_kernel(c.dim, degree, c.system, c.precision);
     size_t tn = 1;
     for (int a = 1; a < c.dim; ++a) tn *= c.NP;
-    size_t stride = 0;
-    for (int a = 0; a < c.dim; ++a)
+    size_t stride = 0, rstride = 0;
+    for (int a = 0; a < c.dim; ++a) {
         stride = std::max(stride, (size_t)c.nblk[a] * (c.cells / c.n[a]) * tn);
+        rstride = std::max(rstride, (size_t)c.tiles[a] * (c.cells / c.n[a]) * tn);
+    }
     c.sig_stride = stride;
+    c.raw_stride = rstride;
 
-    // scratch layout: c64 | c32 | gll | sig0 | raw0 | sig1 | raw1
+    // scratch layout: c64 | c32 | gll | error word | sig0 | raw0 | sig1 | raw1
     const size_t off_c64 = 0;
     const size_t off_c32 = align256(off_c64 + sizeof(double) * 6 * kCoefStride);
     const size_t off_gll = align256(off_c32 + sizeof(float) * 6 * kCoefStride);
-    const size_t off_sum = align256(off_gll + sizeof(double) * 2 * kMaxNP);
+    const size_t off_err = align256(off_gll + sizeof(double) * 2 * kMaxNP);
+    const size_t off_sum = align256(off_err + sizeof(int) * 4);
     const size_t sbytes = align256(stride * c.npop * c.esize);
-    const size_t need = off_sum + 4 * sbytes;
+    const size_t rbytes = align256(rstride * c.npop * c.esize);
+    const size_t need = off_sum + 2 * sbytes + 2 * rbytes;
     if (need > kNoallocScratchBytes) {
         noalloc_msg(errbuf, errlen,
                     "problem needs %zu bytes of scratch; kin_step_noalloc is limited to %zu bytes "
@@ -773,18 +952,17 @@ extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* mo
     c.c64 = reinterpret_cast<double*>(base + off_c64);
     c.coef = c.esize == 4 ? (void*)(base + off_c32) : (void*)c.c64;
     c.gll = reinterpret_cast<double*>(base + off_gll);
+    c.errword = reinterpret_cast<int*>(base + off_err);
     c.sig[0] = base + off_sum;
     c.raw[0] = base + off_sum + sbytes;
-    c.sig[1] = base + off_sum + 2 * sbytes;
-    c.raw[1] = base + off_sum + 3 * sbytes;
+    c.sig[1] = base + off_sum + sbytes + rbytes;
+    c.raw[1] = base + off_sum + 2 * sbytes + rbytes;
     c.cur = 0;
 
-    if (c.smem > 48 * 1024) {
-        e = cudaFuncSetAttribute((const void*)c.kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
-        if (e != cudaSuccess) {
-            noalloc_msg(errbuf, errlen, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
-            return KIN_ECUDA;
-        }
+    e = configure_launch(&c);
+    if (e != cudaSuccess) {
+        noalloc_msg(errbuf, errlen, "launch configuration failed: %s", cudaGetErrorString(e));
+        return KIN_ECUDA;
     }
     SetupArgs sa;
     memset(&sa, 0, sizeof sa);
@@ -799,19 +977,36 @@ extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* mo
     sa.c64 = c.c64;
     sa.c32 = c.esize == 4 ? (float*)c.coef : nullptr;
     sa.gll = c.gll;
-    e = launch_setup(sa, c.stream);
+    // the error word must start at zero; everything else is written before it is read
+    e = cudaMemsetAsync(c.errword, 0, sizeof(int) * 4, c.stream);
+    if (e == cudaSuccess) e = launch_setup(sa, c.stream);
+    // the block-inverse records travel in the launch parameters
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.coef_host, c.c64, sizeof(c.coef_host), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     // summaries of the caller's state, then nsteps full steps (every scratch
     // region is written before it is read, so nothing needs clearing)
     for (int s = 0; e == cudaSuccess && s <= nsteps; ++s) {
         Inst I = make_inst(&c, s == 0 ? 1 : 0);
         void* args[] = {&I};
-        e = cudaLaunchKernel((const void*)c.kfn, dim3(c.grid), dim3(kThreads), args, (size_t)c.smem,
+        e = cudaLaunchKernel((const void*)c.kfn, dim3(c.grid), dim3(c.threads), args, (size_t)c.smem,
                              c.stream);
         c.cur ^= 1;
     }
     if (e != cudaSuccess) {
         noalloc_msg(errbuf, errlen, "kernel launch failed: %s", cudaGetErrorString(e));
         return KIN_ECUDA;
+    }
+    int word = 0;
+    e = cudaMemcpyAsync(&word, c.errword, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) {
+        noalloc_msg(errbuf, errlen, "step failed: %s", cudaGetErrorString(e));
+        return KIN_ECUDA;
+    }
+    if (word) {
+        noalloc_msg(errbuf, errlen, "a bounded device wait ran out (error word 0x%x)", word);
+        return KIN_ETIMEOUT;
     }
     return KIN_OK;
 }

@@ -281,16 +281,19 @@ __global__ void defect_kernel(DefectArgs A, const T* __restrict__ sig, const T* 
         const long long gl = rest % glines;
         const int nb = A.nb[a], NS = A.NS[a], K = A.iters;
         const double RB = c64[k * kCoefStride + kOffRhoB];
-        const long long base = (long long)pop * A.sig_stride + gl;
+        const T* sigp = sig + (long long)pop * A.sig_stride;
+        const T* rawp = raw + (long long)pop * A.raw_stride;
+        // inflow of subdomain S after 'maps' whole upwind subdomains, starting
+        // from the raw outflow value of subdomain S - maps - 1
         auto chain = [&](int maps) {
             int s0 = (S - maps - 1) % NS;
             if (s0 < 0) s0 += NS;
-            double t = (double)raw[base + (long long)(s0 * nb + nb - 1) * glines];
+            double t = (double)rawp[(long long)s0 * glines + gl];
             for (int j = 0; j < maps; ++j) {
                 int sj = (S - maps + j) % NS;
                 if (sj < 0) sj += NS;
                 for (int rr = 0; rr < nb; ++rr)
-                    t = RB * t + (double)sig[base + (long long)(sj * nb + rr) * glines];
+                    t = RB * t + (double)sigp[(long long)(sj * nb + rr) * glines + gl];
             }
             return t;
         };

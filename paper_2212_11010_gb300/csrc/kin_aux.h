@@ -35,6 +35,7 @@ struct DefectArgs {
     long long per_pop[30];   // NS[a] * glines[a] for the population's axis
     long long glines[3];
     long long sig_stride;
+    long long raw_stride;
     int nb[3], NS[3];
     double dt, lambda;
     double h[3];
@@ -50,6 +51,20 @@ cudaError_t launch_mass(const PointArgs& a, const void* f, const double* gll, do
 cudaError_t launch_defect(const DefectArgs& a, const void* sig, const void* raw, const double* c64,
                           const double* gll, double* partial, double* out, int prec,
                           cudaStream_t st);
+
+// A compiled fixed-shape step kernel (see kin_fixed.cuh).
+struct FixedKernel {
+    StepKernel fn;
+    int threads;
+    size_t smem;
+};
+
+// Fixed-shape kernel for (degree, system, precision, block) or fn == nullptr.
+FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3]);
+FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3]);
+// Preferred fixed block shapes for a (dim, degree, system, precision), best first;
+// returns the count written (at most 4).
+int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3]);
 
 // Step kernels, one translation unit per space dimension.
 StepKernel step_kernel_d1(int degree, int system, int prec);

@@ -2,7 +2,9 @@
 //
 // One thread block owns a box of B[0] x B[1] x B[2] cells ("cell block") and
 // every population on it.  A step launch does, per cell block:
-//   1. load f^n of all populations of the block into shared memory;
+//   1. load f^n of all populations of the block into shared memory (bulk
+//      copies of the contiguous rows of B[0] cells, completing on an
+//      mbarrier);
 //   2. transport (Sec. 3.2 downwind algorithm, Sec. 5.1 subdomain iteration):
 //      for an axis-aligned velocity every (cell row, transverse node) line of
 //      the block is an independent 1D recurrence.  Its inflow trace is
@@ -15,7 +17,7 @@
 //   4. block summaries of the relaxed state for the next step: per line, the
 //      outflow trace that the block would produce from a zero inflow
 //      ("sigma") and the raw outflow-node value of the relaxed f ("raw");
-//   5. store f^{n+1}.
+//   5. store f^{n+1} (bulk copies).
 //
 // Why summaries reproduce the K-iteration of eq. ibvp exactly: the outflow
 // trace of a cell is affine in its inflow trace, t_out = prow . u + rho t_in,
@@ -27,20 +29,24 @@
 // where A_j is the affine map of subdomain j (the composition of its blocks'
 // maps) and raw(S-K) the t^n outflow-node value of subdomain S-K (periodic
 // indices).  Inside S, a block's inflow is the composition of the preceding
-// blocks of S applied to that.  This is the same linear algebra as K Jacobi
-// sweeps, so f moves through HBM once per step (read + write) instead of K
-// times.
+// blocks of S applied to that.  In downwind block order this is one flat
+// chain: start from the raw value of the block just before the first block
+// of subdomain S-K+1 and fold in the sigma of every block up to the current
+// one.  This is the same linear algebra as K Jacobi sweeps, so f moves
+// through HBM once per step (read + write) instead of K times.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "kin_tma.cuh"
 
 namespace kin {
 
 constexpr int kAdvection = 0;
 constexpr int kEuler = 1;
 constexpr int kCoefStride = 32;    // coefficient slots per (axis, sign)
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;      // upper bound on threads per block
 
 // coefficient slot layout inside one (axis, sign) record
 //   [0, NP*NP)            Pm = A^{-1} W - I  (row-major)
@@ -53,25 +59,99 @@ constexpr int kOffProw = 20;
 constexpr int kOffRho = 24;
 constexpr int kOffRhoB = 25;
 
+// error word bits (Inst::err)
+constexpr int kErrLoadTimeout = 1;
+
+struct AxisInfo {
+    FastDiv lines;      // lines of one population inside a block: (cells / B_a) * NP^{d-1}
+    FastDiv e1;         // block extent along the first transverse axis
+    long long glines;   // lines of one population in the whole mesh
+};
+
 struct Inst {
     void* f;                 // T*: [pop][cells][nodes], updated in place
     const void* sig_in;      // T*: block summaries of the current state
     const void* raw_in;
     void* sig_out;           // T*: summaries of the state this launch writes
     void* raw_out;
-    const void* coef;        // T*: 2*dim records of kCoefStride
+    int* err;                // device error word (OR of kErr* bits)
     long long nodes;         // cells * nodes per cell
-    long long sig_stride;    // elements per population in sig/raw
+    long long sig_stride;    // elements per population in sig: [block q][line]
+    long long raw_stride;    // elements per population in raw: [S][line]
+    long long wait_cycles;   // bound on the bulk-load wait, in SM clocks
     int n[3];                // cells per axis
     int B[3];                // cell-block extents
     int nblk[3];             // blocks per axis
     int nb[3];               // blocks per subdomain along each axis
     int NS[3];               // subdomains along each axis
+    AxisInfo ax[3];
+    FastDiv fd_nrows;        // B[1] * B[2]
+    FastDiv fd_B1;           // B[1]
+    FastDiv fd_rowlen;       // B[0] * nodes per cell
     int iters;               // K
     int mode;                // 0: full step, 1: summaries only (no transport, no store)
+    int tma;                 // 1: rows moved by bulk copies (alignment checked on the host)
+    int stages;              // shared-memory tile buffers per thread block (1 or 2)
+    int debug_stall;         // test hook: the load barrier expects 16 bytes that never arrive
     double lambda, gamma, omega;
     double adv[3];
+    // block-inverse coefficients (computed in FP64 on the device once per
+    // context), carried in the launch parameters: read from the constant bank
+    double cd[6][kCoefStride];
+    float cf[6][kCoefStride];
 };
+
+template <typename T>
+__device__ __forceinline__ const T* coef_rec(const Inst& I, int dir);
+template <>
+__device__ __forceinline__ const float* coef_rec<float>(const Inst& I, int dir) { return I.cf[dir]; }
+template <>
+__device__ __forceinline__ const double* coef_rec<double>(const Inst& I, int dir) { return I.cd[dir]; }
+
+// Inflow of the final subdomain iterate for the line 'gline' of population
+// 'pop' (axis a, sign sgn) entering block 'bidx' (see the header comment): the
+// raw outflow value of subdomain S-K, then in downwind order the blocks of the
+// K-1 whole subdomains S-K+1 .. S-1 and the blocks of S upwind of this one.
+// Summaries are stored [block q (downwind order)][line], raw values
+// [subdomain][line]; every load is coalesced across consecutive lines.
+template <typename T>
+__device__ __forceinline__ T chain_inflow(const Inst& I, int a, int sgn, int bidx, int pop, long long gline)
+{
+    const int nbk = I.nblk[a], nb = I.nb[a], NS = I.NS[a], K = I.iters;
+    const int q = sgn == 0 ? bidx : nbk - 1 - bidx;
+    const int S = q / nb, r = q - (q / nb) * nb;
+    const long long gl = I.ax[a].glines;
+    const T* __restrict__ sig = static_cast<const T*>(I.sig_in) + (long long)pop * I.sig_stride + gline;
+    const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)pop * I.raw_stride + gline;
+    const T RB = coef_rec<T>(I, 2 * a + sgn)[kOffRhoB];
+    int s0 = S - K;
+    while (s0 < 0) s0 += NS;
+    T t = __ldg(raw + (long long)s0 * gl);
+    const int cnt = (K - 1) * nb + r;
+    int qq = (s0 + 1 == NS) ? 0 : (s0 + 1) * nb;
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j) {
+        t = fma(RB, t, __ldg(sig + (long long)qq * gl));
+        qq = (qq + 1 == nbk) ? 0 : qq + 1;
+    }
+    return t;
+}
+
+// Write the summaries of this block for line 'gline': sigma always, raw only
+// for the downwind-most block of its subdomain.
+template <typename T>
+__device__ __forceinline__ void write_summary(const Inst& I, int a, int sgn, int bidx, int pop, long long gline,
+                                              T sigma, T last)
+{
+    const int nbk = I.nblk[a], nb = I.nb[a];
+    const int q = sgn == 0 ? bidx : nbk - 1 - bidx;
+    const int S = q / nb, r = q - (q / nb) * nb;
+    const long long gl = I.ax[a].glines;
+    T* sig = static_cast<T*>(I.sig_out) + (long long)pop * I.sig_stride;
+    T* raw = static_cast<T*>(I.raw_out) + (long long)pop * I.raw_stride;
+    sig[(long long)q * gl + gline] = sigma;
+    if (r == nb - 1) raw[(long long)S * gl + gline] = last;
+}
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
@@ -98,311 +178,447 @@ struct Acc<double> {
     __device__ __forceinline__ void add(double x) { s += x; }
 };
 
-// Flux Q^a(W) of the conservation law (eq. conslaw): advection a_a u, or the
-// Euler flux of a gamma-law gas.
-template <int D, int SYS, typename T>
-__device__ __forceinline__ void flux(const Inst& I, const T* W, int a, T* Q)
-{
-    if (SYS == kAdvection) {
-        Q[0] = T(I.adv[a]) * W[0];
-    } else {
-        const T rho = W[0];
-        const T inv = T(1) / rho;
-        T ke = 0;
-#pragma unroll
-        for (int b = 0; b < D; ++b) ke += W[1 + b] * W[1 + b];
-        const T E = W[1 + D];
-        const T pr = T(I.gamma - 1.0) * (E - T(0.5) * ke * inv);
-        const T ua = W[1 + a] * inv;
-        Q[0] = W[1 + a];
-#pragma unroll
-        for (int b = 0; b < D; ++b) Q[1 + b] = W[1 + b] * ua + (b == a ? pr : T(0));
-        Q[1 + D] = (E + pr) * ua;
-    }
-}
-
-// Geometry of the lines of one axis inside a cell block.
-template <int D, int NP>
-struct LineGeom {
-    int cs;        // shared-memory stride between consecutive cells along a
-    int ns;        // stride between consecutive nodes along a
-    int base;      // shared-memory offset of the line's first element (pop 0)
-    long long gline;   // global line id within the population's summary slab
-    long long glines;  // lines per summary row for this axis
+// Geometry of one line of axis A inside the block.
+template <int D, int NP, int A>
+struct Line {
+    int base;          // shared-memory offset of the line's first element (population 0)
+    long long gline;   // global line id within a population's summary slab
 };
 
-// Decompose (axis a, local line id) into shared-memory addressing and the
-// global line id.  Local line id = tnode + NP^{D-1} * tcell with tnode the
-// transverse node index and tcell the transverse cell index in the block.
-template <int D, int NP>
-__device__ __forceinline__ LineGeom<D, NP> line_geom(const Inst& I, int a, int line,
-                                                     int bx, int by, int bz)
+template <int D, int NP, int A>
+__device__ __forceinline__ Line<D, NP, A> line_of(const Inst& I, int line, int org0, int org1, int org2)
 {
     constexpr int NN = ipow(NP, D);
     constexpr int TN = ipow(NP, D - 1);
-    const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1;
-    LineGeom<D, NP> G;
+    constexpr int T1 = A == 0 ? 1 : 0;                  // first transverse axis
+    constexpr int T2 = A == 2 ? 1 : 2;                  // second transverse axis
     const int tnode = line % TN;
     const int tcell = line / TN;
     const int jt1 = tnode % NP, jt2 = tnode / NP;
-    int c[3] = {0, 0, 0};   // local cell coordinates (axis a entry = 0)
-    int j[3] = {0, 0, 0};   // node coordinates (axis a entry = 0)
-    int t1 = -1, t2 = -1;   // transverse axes
-    for (int b = 0; b < D; ++b) {
-        if (b == a) continue;
-        if (t1 < 0) t1 = b; else t2 = b;
+    Line<D, NP, A> L;
+    if (D == 1) {
+        L.base = 0;
+        L.gline = 0;
+        return L;
     }
-    if (t1 >= 0) {
-        const int e1 = I.B[t1];
-        c[t1] = tcell % e1;
-        if (t2 >= 0) c[t2] = tcell / e1;
-        j[t1] = jt1;
-        if (t2 >= 0) j[t2] = jt2;
-    }
-    const int cstr[3] = {1, B0, B0 * B1};
-    const int nstr[3] = {1, NP, NP * NP};
-    G.cs = cstr[a] * NN;
-    G.ns = nstr[a];
-    G.base = (c[0] * cstr[0] + c[1] * cstr[1] + c[2] * cstr[2]) * NN + j[0] + j[1] * NP + j[2] * NP * NP;
-    // global transverse cell index: row-major over the transverse axes
-    const int org[3] = {bx * I.B[0], by * (D > 1 ? I.B[1] : 1), bz * (D > 2 ? I.B[2] : 1)};
-    long long gt = 0;
-    if (t2 >= 0) gt = (long long)(org[t2] + c[t2]) * I.n[t1] + (org[t1] + c[t1]);
-    else if (t1 >= 0) gt = org[t1] + c[t1];
-    G.gline = gt * TN + tnode;
-    long long trans_cells = 1;
-    for (int b = 0; b < D; ++b)
-        if (b != a) trans_cells *= I.n[b];
-    G.glines = trans_cells * TN;
-    return G;
+    const unsigned c2 = D == 3 ? fdiv((unsigned)tcell, I.ax[A].e1) : 0u;
+    const unsigned c1 = (unsigned)tcell - c2 * I.ax[A].e1.d;
+    const int B0 = I.B[0], B1 = I.B[1];
+    const int cstr1 = T1 == 0 ? 1 : (T1 == 1 ? B0 : B0 * B1);
+    const int cstr2 = T2 == 1 ? B0 : B0 * B1;
+    constexpr int nstr1 = T1 == 0 ? 1 : (T1 == 1 ? NP : NP * NP);
+    constexpr int nstr2 = T2 == 1 ? NP : NP * NP;
+    L.base = ((int)c1 * cstr1 + (D == 3 ? (int)c2 * cstr2 : 0)) * NN + jt1 * nstr1 + (D == 3 ? jt2 * nstr2 : 0);
+    const int org1v = T1 == 0 ? org0 : (T1 == 1 ? org1 : org2);
+    const int org2v = T2 == 1 ? org1 : org2;
+    long long gt;
+    if (D == 3) gt = (long long)(org2v + (int)c2) * I.n[T1] + (org1v + (int)c1);
+    else gt = org1v + (int)c1;
+    L.gline = gt * TN + tnode;
+    return L;
 }
 
-template <int D>
-__device__ __forceinline__ int items_per_axis(const Inst& I, int a, int NP, int m)
+// Items of axis A: (population of axis A, line) pairs, line fastest.
+template <int D, int P, int SYS, int A>
+__device__ __forceinline__ int items_of_axis(const Inst& I)
 {
-    int bc = 1;
-    for (int b = 0; b < D; ++b) bc *= I.B[b];
-    int tn = 1;
-    for (int b = 1; b < D; ++b) tn *= NP;
-    return 2 * m * (bc / I.B[a]) * tn;
+    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    return 2 * M * (int)I.ax[A].lines.d;
 }
 
-// The fused step on one cell block.  s: dynamic shared memory holding
-// NPOP * cells * NN values of T.
+// Inflow traces of the final subdomain iterate for every item of axis A,
+// folded from the block summaries of the previous launch, into tin[].  These
+// loads do not depend on the tile's own data, so they run while the tile is
+// still being copied in.
+template <int D, int P, int SYS, typename T, int A>
+__device__ __forceinline__ void chain_axis(const Inst& I, int bx, int by, int bz, T* tin)
+{
+    constexpr int NP = P + 1;
+    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
+    const int org0 = bx * B0, org1 = by * B1, org2 = bz * B2;
+    const int Lp = (int)I.ax[A].lines.d;
+    const int items = 2 * M * Lp;
+    const int bidx = A == 0 ? bx : (A == 1 ? by : bz);
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int pl = (int)fdiv((unsigned)it, I.ax[A].lines);
+        const int line = it - pl * Lp;
+        const int sgn = pl / M, v = pl - (pl / M) * M;
+        const int pop = (2 * A + sgn) * M + v;
+        const Line<D, NP, A> G = line_of<D, NP, A>(I, line, org0, org1, org2);
+        const T t = chain_inflow<T>(I, A, sgn, bidx, pop, G.gline);
+        tin[it] = t;
+    }
+}
+
+// Transport (phase 2) or summaries (phase 4) of every line of axis A.
+template <int D, int P, int SYS, typename T, int A, bool SUMMARY>
+__device__ __forceinline__ void lines_axis(const Inst& I, int bx, int by, int bz, T* s, const T* tin)
+{
+    constexpr int NP = P + 1;
+    constexpr int NN = ipow(NP, D);
+    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
+    const int bcells = B0 * B1 * B2;
+    const int org0 = bx * B0, org1 = by * B1, org2 = bz * B2;
+    const int Lp = (int)I.ax[A].lines.d;
+    const int items = 2 * M * Lp;
+    const int cs = (A == 0 ? 1 : (A == 1 ? B0 : B0 * B1)) * NN;
+    constexpr int ns = A == 0 ? 1 : (A == 1 ? NP : NP * NP);
+    const int Ba = I.B[A];
+    const int bidx = A == 0 ? bx : (A == 1 ? by : bz);
+
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int pl = (int)fdiv((unsigned)it, I.ax[A].lines);
+        const int line = it - pl * Lp;
+        const int sgn = pl / M, v = pl - (pl / M) * M;
+        const int pop = (2 * A + sgn) * M + v;
+        const Line<D, NP, A> G = line_of<D, NP, A>(I, line, org0, org1, org2);
+        const T* rec = coef_rec<T>(I, 2 * A + sgn);
+        T* line_p = s + pop * bcells * NN + G.base;
+
+        if (!SUMMARY) {
+            T t = tin[it];
+            T Pm[NP][NP], g[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                g[i] = rec[kOffG + i];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) Pm[i][j] = rec[i * NP + j];
+            }
+#pragma unroll 4
+            for (int cc = 0; cc < Ba; ++cc) {
+                const int c = sgn == 0 ? cc : Ba - 1 - cc;
+                T* p = line_p + c * cs;
+                T u[NP], dlt[NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) u[j] = p[j * ns];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    T acc = Pm[i][0] * u[0];
+#pragma unroll
+                    for (int j = 1; j < NP; ++j) acc = fma(Pm[i][j], u[j], acc);
+                    dlt[i] = fma(g[i], t, acc);     // f* - f^n at node i
+                }
+                t = sgn == 0 ? u[NP - 1] + dlt[NP - 1] : u[0] + dlt[0];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) p[i * ns] = fma(T(2), dlt[i], u[i]);
+            }
+        } else {
+            T prow[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) prow[j] = rec[kOffProw + j];
+            const T rho = rec[kOffRho];
+            T t = 0, last = 0;
+#pragma unroll 4
+            for (int cc = 0; cc < Ba; ++cc) {
+                const int c = sgn == 0 ? cc : Ba - 1 - cc;
+                const T* p = line_p + c * cs;
+                T u[NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) u[j] = p[j * ns];
+                T acc = prow[0] * u[0];
+#pragma unroll
+                for (int j = 1; j < NP; ++j) acc = fma(prow[j], u[j], acc);
+                t = fma(rho, t, acc);
+                last = sgn == 0 ? u[NP - 1] : u[0];
+            }
+            write_summary<T>(I, A, sgn, bidx, pop, G.gline, t, last);
+        }
+    }
+}
+
 template <int D, int P, int SYS, typename T>
-__device__ void step_block(const Inst& I, int bx, int by, int bz, T* s)
+__device__ __forceinline__ void chain_all(const Inst& I, int bx, int by, int bz, T* tin)
+{
+    chain_axis<D, P, SYS, T, 0>(I, bx, by, bz, tin);
+    if constexpr (D > 1) chain_axis<D, P, SYS, T, 1>(I, bx, by, bz, tin + items_of_axis<D, P, SYS, 0>(I));
+    if constexpr (D > 2)
+        chain_axis<D, P, SYS, T, 2>(I, bx, by, bz,
+                                    tin + items_of_axis<D, P, SYS, 0>(I) + items_of_axis<D, P, SYS, 1>(I));
+}
+
+template <int D, int P, int SYS, typename T, bool SUMMARY>
+__device__ __forceinline__ void lines_all(const Inst& I, int bx, int by, int bz, T* s, const T* tin)
+{
+    lines_axis<D, P, SYS, T, 0, SUMMARY>(I, bx, by, bz, s, tin);
+    if constexpr (D > 1)
+        lines_axis<D, P, SYS, T, 1, SUMMARY>(I, bx, by, bz, s, tin + items_of_axis<D, P, SYS, 0>(I));
+    if constexpr (D > 2)
+        lines_axis<D, P, SYS, T, 2, SUMMARY>(I, bx, by, bz, s,
+                                              tin + items_of_axis<D, P, SYS, 0>(I) + items_of_axis<D, P, SYS, 1>(I));
+}
+
+// Relaxation at every node of the block (eq. over_relaxation) with the 2d
+// velocity equilibria M_{a,+-} = W/(2d) +- Q^a(W)/(2 lambda).
+template <int D, int P, int SYS, typename T>
+__device__ __forceinline__ void relax_block(const Inst& I, T* s, int bcells)
 {
     constexpr int NP = P + 1;
     constexpr int NN = ipow(NP, D);
     constexpr int M = SYS == kAdvection ? 1 : D + 2;
     constexpr int NV = 2 * D;
     constexpr int NPOP = NV * M;
-    constexpr int TN = ipow(NP, D - 1);
-
-    const int B0 = I.B[0];
-    const int B1 = D > 1 ? I.B[1] : 1;
-    const int B2 = D > 2 ? I.B[2] : 1;
-    const int bcells = B0 * B1 * B2;
-    const int x0 = bx * B0, y0 = by * B1, z0 = bz * B2;
-    T* __restrict__ f = static_cast<T*>(I.f);
-    const int tid = threadIdx.x;
-    const int nth = blockDim.x;
-
-    // ---- 1. load the block (rows of B0 cells are contiguous in HBM) ----
-    const int rowlen = B0 * NN;
-    const int nrows = B1 * B2;
-    const int nload = NPOP * nrows * rowlen;
-    for (int idx = tid; idx < nload; idx += nth) {
-        const int e = idx % rowlen;
-        const int t = idx / rowlen;
-        const int row = t % nrows;
-        const int pop = t / nrows;
-        const int ly = row % B1, lz = row / B1;
-        const long long g = (long long)pop * I.nodes
-            + (((long long)(z0 + lz) * (D > 1 ? I.n[1] : 1) + (y0 + ly)) * I.n[0] + x0) * NN + e;
-        s[(pop * bcells + row * B0) * NN + e] = f[g];
-    }
-    __syncthreads();
-
-    const T* __restrict__ coef = static_cast<const T*>(I.coef);
-    int ia[3];
-    int total = 0;
+    const int nnodes = bcells * NN;
+    const int pstride = bcells * NN;
+    const T omega = T(I.omega);
+    const bool two = I.omega == 2.0;
+    const T inv2d = T(1.0 / (2.0 * D));
+    const T inv2l = T(1.0 / (2.0 * I.lambda));
+    const T gm1 = T(I.gamma - 1.0);
+    for (int nd = threadIdx.x; nd < nnodes; nd += blockDim.x) {
+        T fk[NPOP];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-        ia[a] = items_per_axis<D>(I, a, NP, M);
-        total += ia[a];
-    }
-
-    // ---- 2. transport of every (population, line) of the block ----
-    if (I.mode == 0) {
-        const T* __restrict__ sig = static_cast<const T*>(I.sig_in);
-        const T* __restrict__ raw = static_cast<const T*>(I.raw_in);
-        for (int item = tid; item < total; item += nth) {
-            int a = 0, it = item;
-            while (it >= ia[a]) { it -= ia[a]; ++a; }
-            const int lines = ia[a] / (2 * M);
-            const int pl = it / lines;
-            const int line = it % lines;
-            const int sgn = pl / M, v = pl % M;
-            const int pop = (2 * a + sgn) * M + v;
-            const LineGeom<D, NP> G = line_geom<D, NP>(I, a, line, bx, by, bz);
-            const int bidx = a == 0 ? bx : (a == 1 ? by : bz);
-            const int nbk = I.nblk[a];
-            const int q = sgn == 0 ? bidx : nbk - 1 - bidx;   // downwind block order
-            const int nb = I.nb[a], NS = I.NS[a];
-            const int S = q / nb, r = q % nb;
-            const T* rec = coef + (2 * a + sgn) * kCoefStride;
-            const T RB = ldc(rec + kOffRhoB);
-            const long long pbase = (long long)pop * I.sig_stride + G.gline;
-            // inflow of the final iterate (see the header comment)
-            int s0 = (S - I.iters) % NS;
-            if (s0 < 0) s0 += NS;
-            T t = raw[pbase + (long long)(s0 * nb + nb - 1) * G.glines];
-            for (int jj = 1; jj < I.iters; ++jj) {
-                int sj = (S - I.iters + jj) % NS;
-                if (sj < 0) sj += NS;
-                for (int rr = 0; rr < nb; ++rr)
-                    t = fma(RB, t, sig[pbase + (long long)(sj * nb + rr) * G.glines]);
-            }
-            for (int rr = 0; rr < r; ++rr)
-                t = fma(RB, t, sig[pbase + (long long)(S * nb + rr) * G.glines]);
-
-            T Pm[NP][NP], g[NP];
+        for (int pp = 0; pp < NPOP; ++pp) fk[pp] = s[pp * pstride + nd];
+        T W[M];
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                g[i] = ldc(rec + kOffG + i);
+        for (int v = 0; v < M; ++v) {
+            Acc<T> acc;
 #pragma unroll
-                for (int j = 0; j < NP; ++j) Pm[i][j] = ldc(rec + i * NP + j);
-            }
-            const int Ba = I.B[a];
-            T* line_p = s + pop * bcells * NN + G.base;
-            for (int cc = 0; cc < Ba; ++cc) {
-                const int c = sgn == 0 ? cc : Ba - 1 - cc;
-                T* p = line_p + c * G.cs;
-                T u[NP], dlt[NP];
-#pragma unroll
-                for (int j = 0; j < NP; ++j) u[j] = p[j * G.ns];
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    T acc = g[i] * t;
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) acc = fma(Pm[i][j], u[j], acc);
-                    dlt[i] = acc;     // f* - f^n at node i
-                }
-                t = sgn == 0 ? u[NP - 1] + dlt[NP - 1] : u[0] + dlt[0];
-#pragma unroll
-                for (int i = 0; i < NP; ++i) p[i * G.ns] = fma(T(2), dlt[i], u[i]);
-            }
+            for (int k = 0; k < NV; ++k) acc.add(fk[k * M + v]);
+            W[v] = acc.s;
         }
-        __syncthreads();
-
-        // ---- 3. relaxation at every node (eq. over_relaxation) ----
-        const int nnodes = bcells * NN;
-        const T omega = T(I.omega);
-        const T inv2d = T(1.0 / (2.0 * D));
-        const T inv2l = T(1.0 / (2.0 * I.lambda));
-        for (int nd = tid; nd < nnodes; nd += nth) {
-            T fk[NPOP];
+        T inv = 0, pr = 0;
+        if (SYS == kEuler) {
+            inv = T(1) / W[0];
+            T ke = 0;
 #pragma unroll
-            for (int pp = 0; pp < NPOP; ++pp) fk[pp] = s[pp * bcells * NN + nd];
-            T W[M];
+            for (int b = 0; b < D; ++b) ke = fma(W[1 + b], W[1 + b], ke);
+            pr = gm1 * (W[1 + D] - T(0.5) * ke * inv);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            T Q[M];
+            if (SYS == kAdvection) {
+                Q[0] = T(I.adv[a]) * W[0];
+            } else {
+                const T ua = W[1 + a] * inv;
+                Q[0] = W[1 + a];
+#pragma unroll
+                for (int b = 0; b < D; ++b) Q[1 + b] = W[1 + b] * ua + (b == a ? pr : T(0));
+                Q[1 + D] = (W[1 + D] + pr) * ua;
+            }
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                Acc<T> acc;
-#pragma unroll
-                for (int k = 0; k < NV; ++k) acc.add(fk[k * M + v]);
-                W[v] = acc.s;
-            }
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                T Q[M];
-                flux<D, SYS, T>(I, W, a, Q);
-#pragma unroll
-                for (int v = 0; v < M; ++v) {
-                    const T base = W[v] * inv2d;
-                    const T half = Q[v] * inv2l;
-                    const T mp = base + half, mm = base - half;
-                    T& fp = fk[(2 * a) * M + v];
-                    T& fm = fk[(2 * a + 1) * M + v];
-                    if (I.omega == 2.0) {
-                        fp = fma(T(2), mp, -fp);
-                        fm = fma(T(2), mm, -fm);
-                    } else {
-                        fp = omega * mp + (T(1) - omega) * fp;
-                        fm = omega * mm + (T(1) - omega) * fm;
-                    }
+                const T base = W[v] * inv2d;
+                const T half = Q[v] * inv2l;
+                T& fp = fk[(2 * a) * M + v];
+                T& fm = fk[(2 * a + 1) * M + v];
+                if (two) {
+                    fp = fma(T(2), base + half, -fp);
+                    fm = fma(T(2), base - half, -fm);
+                } else {
+                    fp = omega * (base + half) + (T(1) - omega) * fp;
+                    fm = omega * (base - half) + (T(1) - omega) * fm;
                 }
             }
-#pragma unroll
-            for (int pp = 0; pp < NPOP; ++pp) s[pp * bcells * NN + nd] = fk[pp];
         }
-        __syncthreads();
-    }
-
-    // ---- 4. block summaries of the (relaxed) state for the next step ----
-    {
-        T* __restrict__ sig = static_cast<T*>(I.sig_out);
-        T* __restrict__ raw = static_cast<T*>(I.raw_out);
-        for (int item = tid; item < total; item += nth) {
-            int a = 0, it = item;
-            while (it >= ia[a]) { it -= ia[a]; ++a; }
-            const int lines = ia[a] / (2 * M);
-            const int pl = it / lines;
-            const int line = it % lines;
-            const int sgn = pl / M, v = pl % M;
-            const int pop = (2 * a + sgn) * M + v;
-            const LineGeom<D, NP> G = line_geom<D, NP>(I, a, line, bx, by, bz);
-            const int bidx = a == 0 ? bx : (a == 1 ? by : bz);
-            const int q = sgn == 0 ? bidx : I.nblk[a] - 1 - bidx;
-            const T* rec = coef + (2 * a + sgn) * kCoefStride;
-            T prow[NP];
 #pragma unroll
-            for (int j = 0; j < NP; ++j) prow[j] = ldc(rec + kOffProw + j);
-            const T rho = ldc(rec + kOffRho);
-            const int Ba = I.B[a];
-            const T* line_p = s + pop * bcells * NN + G.base;
-            T t = 0, last = 0;
-            for (int cc = 0; cc < Ba; ++cc) {
-                const int c = sgn == 0 ? cc : Ba - 1 - cc;
-                const T* p = line_p + c * G.cs;
-                T acc = rho * t;
-#pragma unroll
-                for (int j = 0; j < NP; ++j) acc = fma(prow[j], p[j * G.ns], acc);
-                t = acc;
-                last = sgn == 0 ? p[(NP - 1) * G.ns] : p[0];
-            }
-            const long long o = (long long)pop * I.sig_stride + (long long)q * G.glines + G.gline;
-            sig[o] = t;
-            raw[o] = last;
-        }
-    }
-    (void)TN;
-
-    // ---- 5. store f^{n+1} ----
-    if (I.mode == 0) {
-        for (int idx = tid; idx < nload; idx += nth) {
-            const int e = idx % rowlen;
-            const int t = idx / rowlen;
-            const int row = t % nrows;
-            const int pop = t / nrows;
-            const int ly = row % B1, lz = row / B1;
-            const long long g = (long long)pop * I.nodes
-                + (((long long)(z0 + lz) * (D > 1 ? I.n[1] : 1) + (y0 + ly)) * I.n[0] + x0) * NN + e;
-            f[g] = s[(pop * bcells + row * B0) * NN + e];
-        }
+        for (int pp = 0; pp < NPOP; ++pp) s[pp * pstride + nd] = fk[pp];
     }
 }
 
-template <int D, int P, int SYS, typename T>
-__global__ void __launch_bounds__(kThreads) step_kernel(Inst I)
+// Global offset of row 'row' of population 'pop' of this block.
+template <int D, int NN>
+__device__ __forceinline__ long long row_offset(const Inst& I, int pop, int row, int x0, int y0, int z0)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* s = reinterpret_cast<T*>(smem_raw);
-    const int b = blockIdx.x;
-    const int bx = b % I.nblk[0];
-    const int by = (b / I.nblk[0]) % I.nblk[1];
-    const int bz = b / (I.nblk[0] * I.nblk[1]);
-    step_block<D, P, SYS, T>(I, bx, by, bz, s);
+    int ly = 0, lz = 0;
+    if (D == 2) ly = row;
+    if (D == 3) {
+        lz = (int)fdiv((unsigned)row, I.fd_B1);
+        ly = row - lz * (int)I.fd_B1.d;
+    }
+    const long long cellrow = ((long long)(z0 + lz) * (D > 1 ? I.n[1] : 1) + (y0 + ly)) * I.n[0] + x0;
+    return (long long)pop * I.nodes + cellrow * NN;
+}
+
+struct TileXYZ {
+    int bx, by, bz;
+};
+
+__device__ __forceinline__ TileXYZ tile_xyz(const Inst& I, int t)
+{
+    TileXYZ c;
+    c.bx = t % I.nblk[0];
+    c.by = (t / I.nblk[0]) % I.nblk[1];
+    c.bz = t / (I.nblk[0] * I.nblk[1]);
+    return c;
+}
+
+// Bulk loads of every row of tile t into s, completing on bar (warp 0 only).
+template <int D, int P, int SYS, typename T>
+__device__ __forceinline__ void issue_tile_load(const Inst& I, int t, T* s, uint64_t* bar)
+{
+    constexpr int NN = ipow(P + 1, D);
+    constexpr int NPOP = 2 * D * (SYS == kAdvection ? 1 : D + 2);
+    const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
+    const int bcells = B0 * B1 * B2, rowlen = B0 * NN, nrows = B1 * B2, nchunks = NPOP * nrows;
+    const TileXYZ c = tile_xyz(I, t);
+    const int lane = threadIdx.x;
+    const T* f = static_cast<const T*>(I.f);
+    if (lane == 0)
+        mbar_arrive_expect_tx(bar, (unsigned)(nchunks * rowlen * sizeof(T)) + (I.debug_stall ? 16u : 0u));
+    __syncwarp();
+    for (int ch = lane; ch < nchunks; ch += 32) {
+        const int pop = (int)fdiv((unsigned)ch, I.fd_nrows);
+        const int row = ch - pop * nrows;
+        bulk_g2s(s + (pop * bcells + row * B0) * NN,
+                 f + row_offset<D, NN>(I, pop, row, c.bx * B0, c.by * B1, c.bz * B2),
+                 (unsigned)(rowlen * sizeof(T)), bar);
+    }
+}
+
+// Bulk stores of every row of tile t from s (warp 0 only; one bulk group per lane).
+template <int D, int P, int SYS, typename T>
+__device__ __forceinline__ void issue_tile_store(const Inst& I, int t, const T* s)
+{
+    constexpr int NN = ipow(P + 1, D);
+    constexpr int NPOP = 2 * D * (SYS == kAdvection ? 1 : D + 2);
+    const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
+    const int bcells = B0 * B1 * B2, rowlen = B0 * NN, nrows = B1 * B2, nchunks = NPOP * nrows;
+    const TileXYZ c = tile_xyz(I, t);
+    T* f = static_cast<T*>(I.f);
+    for (int ch = threadIdx.x; ch < nchunks; ch += 32) {
+        const int pop = (int)fdiv((unsigned)ch, I.fd_nrows);
+        const int row = ch - pop * nrows;
+        bulk_s2g(f + row_offset<D, NN>(I, pop, row, c.bx * B0, c.by * B1, c.bz * B2),
+                 s + (pop * bcells + row * B0) * NN, (unsigned)(rowlen * sizeof(T)));
+    }
+    bulk_commit();
+}
+
+// Element-wise load / store of a tile (used when rows are not 16-byte aligned).
+template <int D, int P, int SYS, typename T, bool LOAD>
+__device__ __forceinline__ void copy_tile_generic(const Inst& I, int t, T* s)
+{
+    constexpr int NN = ipow(P + 1, D);
+    constexpr int NPOP = 2 * D * (SYS == kAdvection ? 1 : D + 2);
+    const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
+    const int bcells = B0 * B1 * B2, rowlen = B0 * NN, nrows = B1 * B2;
+    const int nload = NPOP * nrows * rowlen;
+    const TileXYZ c = tile_xyz(I, t);
+    T* f = static_cast<T*>(I.f);
+    for (int idx = threadIdx.x; idx < nload; idx += blockDim.x) {
+        const int ch = (int)fdiv((unsigned)idx, I.fd_rowlen);
+        const int e = idx - ch * rowlen;
+        const int pop = (int)fdiv((unsigned)ch, I.fd_nrows);
+        const int row = ch - pop * nrows;
+        const long long g = row_offset<D, NN>(I, pop, row, c.bx * B0, c.by * B1, c.bz * B2) + e;
+        T& sv = s[(pop * bcells + row * B0) * NN + e];
+        if (LOAD) sv = f[g];
+        else f[g] = sv;
+    }
+}
+
+// Phases 2-4 on a loaded tile; ends after the summaries (no trailing barrier).
+template <int D, int P, int SYS, typename T>
+__device__ __forceinline__ void compute_tile(const Inst& I, int t, T* s, const T* tin)
+{
+    const TileXYZ c = tile_xyz(I, t);
+    const int bcells = I.B[0] * (D > 1 ? I.B[1] : 1) * (D > 2 ? I.B[2] : 1);
+    if (I.mode == 0) {
+        lines_all<D, P, SYS, T, false>(I, c.bx, c.by, c.bz, s, tin);   // 2. transport
+        __syncthreads();
+        relax_block<D, P, SYS, T>(I, s, bcells);                       // 3. relaxation
+        __syncthreads();
+    }
+    lines_all<D, P, SYS, T, true>(I, c.bx, c.by, c.bz, s, tin);        // 4. summaries
+}
+
+template <int D, int P, int SYS, typename T>
+__device__ __forceinline__ void chain_tile(const Inst& I, int t, T* tin)
+{
+    if (I.mode != 0) return;
+    const TileXYZ c = tile_xyz(I, t);
+    chain_all<D, P, SYS, T>(I, c.bx, c.by, c.bz, tin);
+}
+
+// Persistent step kernel: each thread block walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  With bulk copies and two shared-memory stages
+// the load of the next tile and the store of the previous one run while the
+// current tile is computed.
+template <int D, int P, int SYS, typename T>
+__global__ void __launch_bounds__(kThreads) step_kernel(const __grid_constant__ Inst I)
+{
+    constexpr int NN = ipow(P + 1, D);
+    constexpr int NPOP = 2 * D * (SYS == kAdvection ? 1 : D + 2);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int flag;
+    const int bcells = I.B[0] * (D > 1 ? I.B[1] : 1) * (D > 2 ? I.B[2] : 1);
+    T* buf0 = reinterpret_cast<T*>(smem_raw);
+    T* buf1 = buf0 + NPOP * bcells * NN;
+    T* tin = buf0 + I.stages * NPOP * bcells * NN;     // inflow traces of the current tile
+    const int ntiles = I.nblk[0] * I.nblk[1] * I.nblk[2];
+    const int tid = threadIdx.x;
+    const bool warp0 = tid < 32;
+
+    if (!I.tma) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            chain_tile<D, P, SYS, T>(I, t, tin);
+            copy_tile_generic<D, P, SYS, T, true>(I, t, buf0);
+            __syncthreads();
+            compute_tile<D, P, SYS, T>(I, t, buf0, tin);
+            if (I.mode == 0) {
+                __syncthreads();
+                copy_tile_generic<D, P, SYS, T, false>(I, t, buf0);
+            }
+            __syncthreads();
+        }
+        return;
+    }
+
+    int t = blockIdx.x;
+    if (t >= ntiles) return;
+    const bool two = I.stages == 2;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp0) issue_tile_load<D, P, SYS, T>(I, t, buf0, &bar[0]);
+
+    for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
+        const int st = two ? (i & 1) : 0;
+        T* cur = st ? buf1 : buf0;
+        const int tn = t + gridDim.x;
+        if (two && tn < ntiles && warp0) {
+            bulk_wait_read();      // stores of the tile that last used the other stage have read it
+            __syncwarp();
+            issue_tile_load<D, P, SYS, T>(I, tn, st ? buf0 : buf1, &bar[st ^ 1]);
+        }
+        chain_tile<D, P, SYS, T>(I, t, tin);    // overlaps the bulk loads in flight
+        const unsigned parity = two ? ((i >> 1) & 1) : (i & 1);
+        if (tid == 0) flag = mbar_wait_bounded(&bar[st], parity, I.wait_cycles) ? 1 : 0;
+        __syncthreads();
+        if (flag == 0) {
+            // give up: report, wait (bounded) for the copies still in flight, return
+            if (tid == 0) {
+                if (I.err) atomicOr(I.err, kErrLoadTimeout);
+                if (two && tn < ntiles) mbar_wait_bounded(&bar[st ^ 1], ((i + 1) >> 1) & 1, I.wait_cycles);
+            }
+            if (warp0) bulk_wait_all();
+            return;
+        }
+        (void)mbar_try_wait(&bar[st], parity);   // completed phase: acquire for every thread
+
+        compute_tile<D, P, SYS, T>(I, t, cur, tin);
+
+        if (I.mode == 0) {
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (warp0) issue_tile_store<D, P, SYS, T>(I, t, cur);
+        } else {
+            __syncthreads();
+        }
+        if (!two && tn < ntiles && warp0) {
+            bulk_wait_read();
+            __syncwarp();
+            issue_tile_load<D, P, SYS, T>(I, tn, buf0, &bar[0]);
+        }
+    }
+    if (warp0) bulk_wait_all();
 }
 
 }  // namespace kin

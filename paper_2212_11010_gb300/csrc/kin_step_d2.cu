@@ -2,6 +2,7 @@
 // 2 space dimension(s), degrees 1..3, scalar advection and Euler, FP32/FP64.
 #include "kin_aux.h"
 #include "kin_device.cuh"
+#include "kin_fixed.cuh"
 
 namespace kin {
 
@@ -10,6 +11,30 @@ static StepKernel pick(int prec)
 {
     return prec == 1 ? (StepKernel)step_kernel<2, P, SYS, float>
                      : (StepKernel)step_kernel<2, P, SYS, double>;
+}
+
+
+// Fixed shapes compiled for 2D: (degree, system, precision, B0, B1, threads, min blocks per SM).
+#define KIN_FIXED_2D(X)                        \
+    X(1, kEuler, float, 16, 8, 128, 6)         \
+    X(2, kEuler, float, 8, 8, 192, 5)          \
+    X(3, kEuler, float, 8, 4, 128, 6)          \
+    X(2, kEuler, double, 8, 8, 192, 3)
+
+FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3])
+{
+    FixedKernel k{nullptr, 0, 0};
+#define KIN_TRY(PP, SY, TT, X0, X1, NT, MB)                                                        \
+    if (degree == PP && system == SY && prec == (sizeof(TT) == 4 ? 1 : 0) && B[0] == X0 && B[1] == X1 && \
+        B[2] == 1) {                                                                                \
+        k.fn = (StepKernel)step_kernel_fixed<2, PP, SY, TT, X0, X1, 1, NT, MB>;                       \
+        k.threads = NT;                                                                             \
+        k.smem = Shape<2, PP, SY, TT, X0, X1, 1>::SMEM;                                              \
+        return k;                                                                                   \
+    }
+    KIN_FIXED_2D(KIN_TRY)
+#undef KIN_TRY
+    return k;
 }
 
 StepKernel step_kernel_d2(int degree, int system, int prec)

@@ -2,6 +2,7 @@
 // 3 space dimension(s), degrees 1..3, scalar advection and Euler, FP32/FP64.
 #include "kin_aux.h"
 #include "kin_device.cuh"
+#include "kin_fixed.cuh"
 
 namespace kin {
 
@@ -10,6 +11,57 @@ static StepKernel pick(int prec)
 {
     return prec == 1 ? (StepKernel)step_kernel<3, P, SYS, float>
                      : (StepKernel)step_kernel<3, P, SYS, double>;
+}
+
+
+// Fixed shapes compiled for 3D: (degree, system, precision, B0, B1, B2, threads, min blocks per SM).
+#define KIN_FIXED_3D(X)                          \
+    X(1, kEuler, float, 8, 2, 2, 128, 6)         \
+    X(1, kEuler, float, 4, 4, 2, 128, 6)         \
+    X(1, kEuler, float, 8, 4, 2, 256, 3)         \
+    X(1, kEuler, float, 4, 4, 4, 320, 3)
+
+FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3])
+{
+    FixedKernel k{nullptr, 0, 0};
+#define KIN_TRY(PP, SY, TT, X0, X1, X2, NT, MB)                                                    \
+    if (degree == PP && system == SY && prec == (sizeof(TT) == 4 ? 1 : 0) && B[0] == X0 && B[1] == X1 && \
+        B[2] == X2) {                                                                               \
+        k.fn = (StepKernel)step_kernel_fixed<3, PP, SY, TT, X0, X1, X2, NT, MB>;                      \
+        k.threads = NT;                                                                             \
+        k.smem = Shape<3, PP, SY, TT, X0, X1, X2>::SMEM;                                             \
+        return k;                                                                                   \
+    }
+    KIN_FIXED_3D(KIN_TRY)
+#undef KIN_TRY
+    return k;
+}
+
+int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3])
+{
+    int n = 0;
+    auto add = [&](int a, int b, int c) {
+        if (n < 4) {
+            out[n][0] = a;
+            out[n][1] = b;
+            out[n][2] = c;
+            ++n;
+        }
+    };
+    if (system != kEuler) return 0;
+    if (dim == 2 && prec == 1) {
+        if (degree == 1) add(16, 8, 1);
+        if (degree == 2) add(8, 8, 1);
+        if (degree == 3) add(8, 4, 1);
+    }
+    if (dim == 2 && prec == 0 && degree == 2) add(8, 8, 1);
+    if (dim == 3 && prec == 1 && degree == 1) {
+        add(4, 4, 2);
+        add(4, 4, 4);
+        add(8, 2, 2);
+        add(8, 4, 2);
+    }
+    return n;
 }
 
 StepKernel step_kernel_d3(int degree, int system, int prec)

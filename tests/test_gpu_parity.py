@@ -220,8 +220,9 @@ def test_constant_state_preserved(kin):
     w = workloads.with_(w, W0=W0, tiles=(2, 2, 2))
     for prec in (kin.KIN_FP64, kin.KIN_FP32):
         W, _, _ = gpu_run(kin, w, 5, precision=prec)
-        tol = 1e-14 if prec == kin.KIN_FP64 else 1e-6
-        assert np.abs(W - W0.reshape(-1)).max() < tol
+        # exact in exact arithmetic; rounding only (relative to max |W|)
+        tol = 1e-14 if prec == kin.KIN_FP64 else TOL32
+        assert np.abs(W - W0.reshape(-1)).max() / np.abs(W0).max() < tol
 
 
 def test_runtime_errors_are_reported(kin):
@@ -263,3 +264,28 @@ def test_torch_allocator_and_device_buffers(kin):
     W_host, _, _ = gpu_run(kin, w, 2)
     assert np.array_equal(out.cpu().numpy(), W_host)
     ctx.close()
+
+
+def test_bounded_load_wait_reports_timeout_and_gpu_stays_usable(kin):
+    # The test hook makes every thread block's bulk-load barrier expect 16
+    # bytes that never arrive; the block's wait gives up after the short
+    # limit, sets the device error word and returns.  The host reports
+    # KIN_ETIMEOUT at the next synchronising call, the context is poisoned,
+    # and a fresh context on the same device still computes correctly.
+    w = workloads.vortex2d(seed=3, n=16, degree=2, tiles=2)
+    w = workloads.with_(w, tiles=(2, 2))
+    ctx = kin.Context.from_workload(w, block=(8, 8), wait_timeout_s=0.002,
+                                    debug_flags=kin.KIN_DEBUG_STALL_LOAD)
+    with pytest.raises(kin.KinError) as ei:
+        ctx.set_state(w.W0.reshape(-1).copy())
+        ctx.step(1)
+        ctx.sync()
+    assert ei.value.status == kin.KIN_ETIMEOUT
+    with pytest.raises(kin.KinError) as ei:
+        ctx.step(1)
+    assert ei.value.status == kin.KIN_ESTATE
+    ctx.close()
+    W, _, _ = gpu_run(kin, w, 2, block=(8, 8))
+    _, Wo = oracle_run(w, 2)
+    l2, linf = rel_errors(w, W, Wo)
+    assert l2 < TOL32 and linf < TOL32
