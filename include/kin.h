@@ -207,6 +207,32 @@ kin_status kin_diag(kin_ctx* ctx, double* mass_per_var, double* next_defect, dou
 kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int degree, double dt,
                             const kin_opts* opts, void* f, int nsteps, char* errbuf, size_t errlen);
 
+/* Batched stepping of several independent problems (the paper's method
+ * applied to each; Sec. 2.2, 3, 5.1).  A batch groups existing contexts with
+ * a state; kin_batch_step advances every member by nsteps steps with, per
+ * step, one persistent launch per kernel type covering the tiles of all
+ * members of that type (problems of different mesh size share a launch),
+ * replayed from a captured CUDA graph.  Results equal stepping each member
+ * alone (bitwise: the same kernel arithmetic per tile).
+ *
+ * members: count distinct contexts of one device, each with a state; they
+ * stay owned by the caller and must outlive the batch.  stream: cudaStream_t
+ * of the batch (NULL = a stream the batch creates and owns; the legacy
+ * default stream cannot hold the captured graphs); work already queued on a
+ * member's stream runs before the batch step, and later work on it after.
+ * Stepping a member alone while it is in a batch invalidates the batch
+ * (KIN_ESTATE on the next kin_batch_step).  Errors: KIN_EINVAL (bad
+ * arguments), KIN_ESTATE (member without state / poisoned / stepped alone),
+ * KIN_ECUDA, KIN_ENOMEM; messages from kin_batch_last_error. */
+typedef struct kin_batch kin_batch;
+kin_status kin_batch_create(kin_ctx* const* members, int count, void* stream, kin_batch** out);
+kin_status kin_batch_step(kin_batch* batch, int nsteps);
+kin_status kin_batch_sync(kin_batch* batch);
+kin_status kin_batch_destroy(kin_batch* batch);
+/* Message of the last error of this batch (or of the last failed
+ * kin_batch_create on this thread when batch is NULL); never NULL. */
+const char* kin_batch_last_error(const kin_batch* batch);
+
 /* Block the host until the context's queued work is done. */
 kin_status kin_sync(kin_ctx* ctx);
 

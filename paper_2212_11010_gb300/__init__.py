@@ -32,7 +32,8 @@ STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
 
 EXPORTED = ["kin_create", "kin_set_state", "kin_set_kinetic", "kin_step", "kin_get_state",
             "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error",
-            "kin_step_noalloc"]
+            "kin_step_noalloc", "kin_batch_create", "kin_batch_step", "kin_batch_sync",
+            "kin_batch_destroy", "kin_batch_last_error"]
 
 
 class KinError(RuntimeError):
@@ -103,10 +104,16 @@ def load_library():
     lib.kin_step_noalloc.argtypes = [ctypes.POINTER(kin_mesh), ctypes.POINTER(kin_model), ctypes.c_int,
                                      ctypes.c_double, ctypes.POINTER(kin_opts), vp, ctypes.c_int,
                                      ctypes.c_char_p, sz]
+    lib.kin_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.kin_batch_step.argtypes = [vp, ctypes.c_int]
+    lib.kin_batch_sync.argtypes = [vp]
+    lib.kin_batch_destroy.argtypes = [vp]
+    lib.kin_batch_last_error.argtypes = [vp]
+    lib.kin_batch_last_error.restype = ctypes.c_char_p
     lib.kin_last_error.argtypes = [vp]
     lib.kin_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name != "kin_last_error":
+        if name not in ("kin_last_error", "kin_batch_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -233,6 +240,36 @@ def kin_step_noalloc(mesh: kin_mesh, model: kin_model, degree: int, dt: float, o
         raise KinError(st, err.value.decode())
 
 
+def _bcheck(batch, status):
+    if status != KIN_OK:
+        raise KinError(status, load_library().kin_batch_last_error(batch).decode())
+
+
+def kin_batch_create(ctxs, stream=None):
+    """Batch of contexts stepped together (one launch per kernel type per step)."""
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    out = ctypes.c_void_p()
+    _bcheck(None, lib.kin_batch_create(arr, len(ctxs), stream, ctypes.byref(out)))
+    return out
+
+
+def kin_batch_step(batch, nsteps: int):
+    _bcheck(batch, load_library().kin_batch_step(batch, nsteps))
+
+
+def kin_batch_sync(batch):
+    _bcheck(batch, load_library().kin_batch_sync(batch))
+
+
+def kin_batch_destroy(batch):
+    _bcheck(None, load_library().kin_batch_destroy(batch))
+
+
+def kin_batch_last_error(batch=None) -> str:
+    return load_library().kin_batch_last_error(batch).decode()
+
+
 def kin_last_error(ctx=None) -> str:
     return load_library().kin_last_error(ctx).decode()
 
@@ -264,6 +301,37 @@ def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 
         opts.alloc = a
         opts.free = f
     return mesh, model, opts
+
+
+class Batch:
+    """Owning wrapper of a kin_batch over Context objects (which must outlive it)."""
+
+    def __init__(self, contexts, stream=None):
+        self.contexts = list(contexts)
+        self.handle = kin_batch_create([c.ctx for c in self.contexts], stream)
+
+    def step(self, n=1):
+        kin_batch_step(self.handle, n)
+
+    def sync(self):
+        kin_batch_sync(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            kin_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Context:

@@ -150,12 +150,9 @@ static void choose_block(const kin_ctx* c, int B[3])
     const int ns = fixed_shapes(c->dim, c->degree, c->system, c->precision, shapes);
     for (int k = 0; k < ns; ++k) {
         bool fits = true;
-        long long tiles = 1;
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < 3; ++a)
             if (c->L[a] % shapes[k][a]) fits = false;
-            tiles *= c->n[a] / shapes[k][a];
-        }
-        if (fits && tiles >= 152) {
+        if (fits) {
             for (int a = 0; a < 3; ++a) B[a] = shapes[k][a];
             return;
         }
@@ -290,7 +287,7 @@ static cudaError_t configure_launch(kin_ctx* c)
     const size_t tin = ((size_t)(items[0] + items[1] + items[2]) * c->esize + 15) & ~size_t(15);
     const bool tma = rows_are_16b_aligned(c);
     // fixed-shape kernel: same result, compile-time shape (bulk copies, one stage)
-    FixedKernel fk{nullptr, 0, 0};
+    FixedKernel fk{nullptr, nullptr, 0, 0};
     if (c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B);
     if (c->dim == 3) fk = fixed_kernel_d3(c->degree, c->system, c->precision, c->B);
     c->fixed = fk.fn && tma && (c->want_threads == 0 || c->want_threads == fk.threads) && c->want_stages != 2;
@@ -754,6 +751,285 @@ const char* kin_last_error(const kin_ctx* c)
 }
 
 }  // extern "C"
+
+
+// ---------------------------------------------------------------------------
+// batches of independent problems
+// ---------------------------------------------------------------------------
+
+struct kin_batch {
+    struct Group {
+        const void* fn = nullptr;
+        int threads = 0, grid = 0;
+        size_t smem = 0;
+        std::vector<int> members;     // indices into kin_batch::members
+        int nwork = 0;
+        Inst* insts[2] = {nullptr, nullptr};   // launch records for summary parity 0 / 1
+        int2* work = nullptr;
+    };
+    std::vector<kin_ctx*> members;
+    std::vector<int> expect_cur;      // members' summary parity at batch parity 0
+    std::vector<int> solo;            // members stepped by their own kernel
+    std::vector<Group> groups;
+    std::vector<void*> dev;           // device allocations of the batch
+    std::vector<cudaEvent_t> ev_member;
+    cudaEvent_t ev_done = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;          // created here because the caller passed NULL
+    cudaGraphExec_t g2[2] = {nullptr, nullptr};   // two steps starting at parity q
+    cudaGraphExec_t g1[2] = {nullptr, nullptr};   // one step at parity q
+    int parity = 0;
+    std::string err = "no error";
+};
+
+static thread_local std::string g_batch_error = "no error";
+
+static kin_status batch_fail(kin_batch* b, kin_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_batch_error = buf;
+    return st;
+}
+
+static void batch_release(kin_batch* b)
+{
+    for (int q = 0; q < 2; ++q) {
+        if (b->g2[q]) cudaGraphExecDestroy(b->g2[q]);
+        if (b->g1[q]) cudaGraphExecDestroy(b->g1[q]);
+    }
+    for (auto e : b->ev_member)
+        if (e) cudaEventDestroy(e);
+    if (b->ev_done) cudaEventDestroy(b->ev_done);
+    for (void* p : b->dev) cudaFree(p);
+    b->dev.clear();
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    b->stream = nullptr;
+}
+
+// Enqueue one batch step at summary parity q (members' cur = expect_cur ^ q).
+static cudaError_t batch_enqueue_step(kin_batch* b, int q)
+{
+    for (auto& g : b->groups) {
+        const Inst* insts = g.insts[q];
+        const int2* work = g.work;
+        int nwork = g.nwork;
+        void* args[] = {(void*)&insts, (void*)&work, (void*)&nwork};
+        cudaError_t e = cudaLaunchKernel(g.fn, dim3(g.grid), dim3(g.threads), args, g.smem, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    for (int mi : b->solo) {
+        kin_ctx* c = b->members[mi];
+        const int saved = c->cur;
+        c->cur = b->expect_cur[mi] ^ q;
+        Inst I = make_inst(c, 0);
+        c->cur = saved;
+        void* args[] = {&I};
+        cudaError_t e = cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(c->threads), args,
+                                         (size_t)c->smem, b->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t batch_capture(kin_batch* b, int q, int nsteps, cudaGraphExec_t* out)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t el = cudaSuccess;
+    for (int s = 0; s < nsteps && el == cudaSuccess; ++s) el = batch_enqueue_step(b, q ^ (s & 1));
+    e = cudaStreamEndCapture(b->stream, &graph);
+    if (el != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return el;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+extern "C" kin_status kin_batch_create(kin_ctx* const* members, int count, void* stream, kin_batch** out)
+{
+    if (!out) return batch_fail(nullptr, KIN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!members || count < 1) return batch_fail(nullptr, KIN_EINVAL, "need at least one member");
+    for (int i = 0; i < count; ++i) {
+        if (!members[i]) return batch_fail(nullptr, KIN_EINVAL, "member %d is NULL", i);
+        if (members[i]->poisoned) return batch_fail(nullptr, KIN_ESTATE, "member %d is poisoned", i);
+        if (!members[i]->have_state) return batch_fail(nullptr, KIN_ESTATE, "member %d has no state", i);
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return batch_fail(nullptr, KIN_EINVAL, "member %d repeats member %d", i, j);
+    }
+    kin_batch* b = new (std::nothrow) kin_batch();
+    if (!b) return batch_fail(nullptr, KIN_ENOMEM, "host allocation failed");
+    b->stream = (cudaStream_t)stream;
+    if (!b->stream) {
+        // graphs cannot be captured on the legacy default stream
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return batch_fail(nullptr, KIN_ECUDA, "could not create the batch stream");
+        }
+        b->own_stream = true;
+    }
+    b->members.assign(members, members + count);
+    for (auto* c : b->members) b->expect_cur.push_back(c->cur);
+
+    // group the members that run a fixed-shape kernel by kernel
+    for (int i = 0; i < count; ++i) {
+        kin_ctx* c = b->members[i];
+        FixedKernel fk{nullptr, nullptr, 0, 0};
+        if (c->fixed && c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B);
+        if (c->fixed && c->dim == 3) fk = fixed_kernel_d3(c->degree, c->system, c->precision, c->B);
+        if (!fk.batch_fn) {
+            b->solo.push_back(i);
+            continue;
+        }
+        kin_batch::Group* g = nullptr;
+        for (auto& gg : b->groups)
+            if (gg.fn == fk.batch_fn) g = &gg;
+        if (!g) {
+            b->groups.emplace_back();
+            g = &b->groups.back();
+            g->fn = fk.batch_fn;
+            g->threads = fk.threads;
+            g->smem = fk.smem;
+        }
+        g->members.push_back(i);
+    }
+
+    cudaError_t e = cudaSuccess;
+    int dev = 0, nsm = 1;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    for (auto& g : b->groups) {
+        if (e != cudaSuccess) break;
+        std::vector<Inst> h[2];
+        std::vector<int2> work;
+        for (size_t k = 0; k < g.members.size(); ++k) {
+            kin_ctx* c = b->members[g.members[k]];
+            const int saved = c->cur;
+            for (int q = 0; q < 2; ++q) {
+                c->cur = b->expect_cur[g.members[k]] ^ q;
+                h[q].push_back(make_inst(c, 0));
+            }
+            c->cur = saved;
+            const int ntiles = c->nblk[0] * c->nblk[1] * c->nblk[2];
+            for (int t = 0; t < ntiles; ++t) work.push_back(make_int2((int)k, t));
+        }
+        g.nwork = (int)work.size();
+        if (g.smem > 48 * 1024)
+            e = cudaFuncSetAttribute(g.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(g.fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int occ = 1;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g.fn, g.threads, g.smem);
+        g.grid = (int)std::min<long long>(g.nwork, (long long)std::max(occ, 1) * nsm);
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+            void* p = nullptr;
+            e = cudaMalloc(&p, sizeof(Inst) * h[q].size());
+            if (e == cudaSuccess) {
+                b->dev.push_back(p);
+                g.insts[q] = (Inst*)p;
+                e = cudaMemcpy(p, h[q].data(), sizeof(Inst) * h[q].size(), cudaMemcpyHostToDevice);
+            }
+        }
+        if (e == cudaSuccess) {
+            void* p = nullptr;
+            e = cudaMalloc(&p, sizeof(int2) * work.size());
+            if (e == cudaSuccess) {
+                b->dev.push_back(p);
+                g.work = (int2*)p;
+                e = cudaMemcpy(p, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice);
+            }
+        }
+    }
+    b->ev_member.assign(count, nullptr);
+    for (int i = 0; i < count && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&b->ev_member[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+        e = batch_capture(b, q, 2, &b->g2[q]);
+        if (e == cudaSuccess) e = batch_capture(b, q, 1, &b->g1[q]);
+    }
+    if (e != cudaSuccess) {
+        kin_status st = batch_fail(nullptr, e == cudaErrorMemoryAllocation ? KIN_ENOMEM : KIN_ECUDA,
+                                   "batch set-up failed: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        batch_release(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return KIN_OK;
+}
+
+extern "C" kin_status kin_batch_step(kin_batch* b, int nsteps)
+{
+    if (!b) return KIN_EINVAL;
+    if (nsteps < 0) return batch_fail(b, KIN_EINVAL, "nsteps must be >= 0");
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        kin_ctx* c = b->members[i];
+        if (c->poisoned) return batch_fail(b, KIN_ESTATE, "member %zu is poisoned", i);
+        if (c->cur != (b->expect_cur[i] ^ b->parity))
+            return batch_fail(b, KIN_ESTATE, "member %zu was stepped outside the batch", i);
+    }
+    if (nsteps == 0) return KIN_OK;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(b->ev_member[i], b->members[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_member[i], 0);
+    }
+    int left = nsteps;
+    while (e == cudaSuccess && left >= 2) {
+        e = cudaGraphLaunch(b->g2[b->parity], b->stream);
+        left -= 2;
+    }
+    if (e == cudaSuccess && left == 1) {
+        e = cudaGraphLaunch(b->g1[b->parity], b->stream);
+        b->parity ^= 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_done, b->stream);
+    for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i)
+        e = cudaStreamWaitEvent(b->members[i]->stream, b->ev_done, 0);
+    if (e != cudaSuccess) return batch_fail(b, KIN_ECUDA, "batch step failed: %s", cudaGetErrorString(e));
+    for (auto* c : b->members) {
+        if (nsteps & 1) c->cur ^= 1;
+        c->steps_done += nsteps;
+    }
+    return KIN_OK;
+}
+
+extern "C" kin_status kin_batch_sync(kin_batch* b)
+{
+    if (!b) return KIN_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, KIN_ECUDA, "batch sync failed: %s", cudaGetErrorString(e));
+    for (size_t i = 0; i < b->members.size(); ++i) {
+        kin_status st = check_errword(b->members[i]);
+        if (st) return batch_fail(b, st, "member %zu: %s", i, b->members[i]->err.c_str());
+    }
+    return KIN_OK;
+}
+
+extern "C" kin_status kin_batch_destroy(kin_batch* b)
+{
+    if (!b) return KIN_OK;
+    cudaStreamSynchronize(b->stream);
+    batch_release(b);
+    delete b;
+    return KIN_OK;
+}
+
+extern "C" const char* kin_batch_last_error(const kin_batch* b)
+{
+    return b ? b->err.c_str() : g_batch_error.c_str();
+}
 
 // ---------------------------------------------------------------------------
 // kin_step_noalloc: the step kernels with their scratch in a static device

@@ -54,7 +54,8 @@ cudaError_t launch_defect(const DefectArgs& a, const void* sig, const void* raw,
 
 // A compiled fixed-shape step kernel (see kin_fixed.cuh).
 struct FixedKernel {
-    StepKernel fn;
+    StepKernel fn;           // single problem: fn(Inst)
+    const void* batch_fn;    // several problems: batch_fn(const Inst*, const int2*, int)
     int threads;
     size_t smem;
 };

@@ -68,7 +68,7 @@ struct AxisInfo {
     long long glines;   // lines of one population in the whole mesh
 };
 
-struct Inst {
+struct __align__(16) Inst {
     void* f;                 // T*: [pop][cells][nodes], updated in place
     const void* sig_in;      // T*: block summaries of the current state
     const void* raw_in;

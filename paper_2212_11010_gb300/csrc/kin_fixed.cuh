@@ -363,6 +363,51 @@ __device__ __forceinline__ void fixed_issue_copies(const Inst& I, int org0, int 
     if (STORE) bulk_commit();
 }
 
+// One tile of the fixed-shape step: issue the bulk loads, fold the look-back
+// inflows while they fly, wait (bounded), sweep, relax, write the summaries
+// and issue the bulk stores.  'i' counts the tiles this thread block has
+// processed (mbarrier phase).  Returns false if the bounded wait gave up.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
+__device__ __forceinline__ bool fixed_tile(const Inst& I, int t, int i, T* s, uint64_t* bar, int* flag,
+                                           T (&tr)[3][KM])
+{
+    const int tid = threadIdx.x;
+    const bool warp0 = tid < 32;
+    const TileXYZ c = tile_xyz(I, t);
+    const int org0 = c.bx * B0, org1 = c.by * B1, org2 = c.bz * B2;
+    if (warp0) {
+        if (i > 0) {
+            bulk_wait_read();   // previous tile's stores have read the buffer
+            __syncwarp();
+        }
+        fixed_issue_copies<D, P, SYS, T, B0, B1, B2, false>(I, org0, org1, org2, s, bar);
+    }
+    if (I.mode == 0) fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 0, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
+    if (tid == 0) *flag = mbar_wait_bounded(bar, i & 1, I.wait_cycles) ? 1 : 0;
+    __syncthreads();
+    if (*flag == 0) {
+        // give up: report, wait (bounded) for the copies still in flight
+        if (tid == 0) {
+            if (I.err) atomicOr(I.err, kErrLoadTimeout);
+            mbar_wait_bounded(bar, i & 1, I.wait_cycles);
+        }
+        if (warp0) bulk_wait_all();
+        return false;
+    }
+    (void)mbar_try_wait(bar, i & 1);
+    if (I.mode == 0) {
+        fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 1, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
+        __syncthreads();
+        fixed_relax<D, P, SYS, T, B0, B1, B2, NTH>(I, s);
+        __syncthreads();
+    }
+    fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 2, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
+    if (I.mode == 0) fence_proxy_async_smem();
+    __syncthreads();
+    if (I.mode == 0 && warp0) fixed_issue_copies<D, P, SYS, T, B0, B1, B2, true>(I, org0, org1, org2, s, bar);
+    return true;
+}
+
 // Fixed-shape step kernel: one tile per loop iteration, one shared-memory
 // stage; the grid is persistent (blocks walk tiles blockIdx.x + k gridDim.x).
 template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MINB>
@@ -376,50 +421,55 @@ __global__ void __launch_bounds__(NTH, MINB) step_kernel_fixed(const __grid_cons
     constexpr int KM = S::kpt_max(NTH / 2);
     T tr[3][KM];      // look-back inflows of this thread's lines
     const int ntiles = I.nblk[0] * I.nblk[1] * I.nblk[2];
-    const int tid = threadIdx.x;
-    const bool warp0 = tid < 32;
     int t = blockIdx.x;
     if (t >= ntiles) return;
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
-        const TileXYZ c = tile_xyz(I, t);
-        const int org0 = c.bx * B0, org1 = c.by * B1, org2 = c.bz * B2;
-        if (warp0) {
-            if (i > 0) {
-                bulk_wait_read();   // previous tile's stores have read the buffer
-                __syncwarp();
-            }
-            fixed_issue_copies<D, P, SYS, T, B0, B1, B2, false>(I, org0, org1, org2, s, &bar);
-        }
-        if (I.mode == 0) fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 0, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
-        if (tid == 0) flag = mbar_wait_bounded(&bar, i & 1, I.wait_cycles) ? 1 : 0;
-        __syncthreads();
-        if (flag == 0) {
-            // give up: report, wait (bounded) for the copies still in flight, return
-            if (tid == 0) {
-                if (I.err) atomicOr(I.err, kErrLoadTimeout);
-                mbar_wait_bounded(&bar, i & 1, I.wait_cycles);
-            }
-            if (warp0) bulk_wait_all();
-            return;
-        }
-        (void)mbar_try_wait(&bar, i & 1);
-        if (I.mode == 0) {
-            fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 1, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
-            __syncthreads();
-            fixed_relax<D, P, SYS, T, B0, B1, B2, NTH>(I, s);
-            __syncthreads();
-        }
-        fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 2, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
-        if (I.mode == 0) fence_proxy_async_smem();
-        __syncthreads();
-        if (I.mode == 0 && warp0) fixed_issue_copies<D, P, SYS, T, B0, B1, B2, true>(I, org0, org1, org2, s, &bar);
+    for (int i = 0; t < ntiles; ++i, t += gridDim.x)
+        if (!fixed_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, t, i, s, &bar, &flag, tr)) return;
+    if (threadIdx.x < 32) bulk_wait_all();
+}
+
+// Batched fixed-shape step kernel: the thread blocks walk a work list of
+// (instance, tile) pairs over several independent problems of the same
+// kernel type; each instance's launch record is copied into shared memory
+// when a block moves to a tile of another instance.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB)
+    step_kernel_fixed_batch(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork)
+{
+    using S = Shape<D, P, SYS, T, B0, B1, B2>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int flag;
+    __shared__ __align__(16) Inst Ish;
+    T* s = reinterpret_cast<T*>(smem_raw);
+    constexpr int KM = S::kpt_max(NTH / 2);
+    T tr[3][KM];
+    int w = blockIdx.x;
+    if (w >= nwork) return;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
     }
-    if (warp0) bulk_wait_all();
+    int have = -1;
+    for (int i = 0; w < nwork; ++i, w += gridDim.x) {
+        const int2 wk = work[w];
+        if (wk.x != have) {
+            // warp 0 may still read the record while issuing the previous tile's stores
+            __syncthreads();
+            const int4* src = reinterpret_cast<const int4*>(insts + wk.x);
+            int4* dst = reinterpret_cast<int4*>(&Ish);
+            for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 16); k += NTH) dst[k] = src[k];
+            have = wk.x;
+        }
+        __syncthreads();
+        if (!fixed_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(Ish, wk.y, i, s, &bar, &flag, tr)) return;
+    }
+    if (threadIdx.x < 32) bulk_wait_all();
 }
 
 }  // namespace kin

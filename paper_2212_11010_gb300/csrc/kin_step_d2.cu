@@ -23,11 +23,12 @@ static StepKernel pick(int prec)
 
 FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3])
 {
-    FixedKernel k{nullptr, 0, 0};
+    FixedKernel k{nullptr, nullptr, 0, 0};
 #define KIN_TRY(PP, SY, TT, X0, X1, NT, MB)                                                        \
     if (degree == PP && system == SY && prec == (sizeof(TT) == 4 ? 1 : 0) && B[0] == X0 && B[1] == X1 && \
         B[2] == 1) {                                                                                \
         k.fn = (StepKernel)step_kernel_fixed<2, PP, SY, TT, X0, X1, 1, NT, MB>;                       \
+        k.batch_fn = (const void*)step_kernel_fixed_batch<2, PP, SY, TT, X0, X1, 1, NT, MB>;          \
         k.threads = NT;                                                                             \
         k.smem = Shape<2, PP, SY, TT, X0, X1, 1>::SMEM;                                              \
         return k;                                                                                   \

