@@ -340,6 +340,135 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _events_time(stream, fn, steps):
+    import torch
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(steps):
+        fn()
+    e.record(stream)
+    e.synchronize()
+    return s.elapsed_time(e) / 1e3
+
+
+def run_batched(args):
+    """64 uneven 2D Euler / D2Q4 instances (n in {64,128,256,512}, p in
+    {1,2,3}, vortex or density wave, dt multiple in [2,8]) stepped together in
+    FP32 (one launch per degree per step, CUDA graphs), against the same
+    instances in FP64 stepped one instance at a time.  The state (3.4 GB FP32)
+    exceeds L2, so no flush is needed between steps."""
+    import torch
+    import workloads
+    import paper_2212_11010_gb300 as kin
+    from paper_2212_11010_gb300 import build as kbuild
+    ws, rank, _ = dist_env()
+    torch.cuda.set_device(0)
+    if not kbuild.up_to_date():
+        kbuild.build()
+    kin.load_library()
+    mix = workloads.batched_mix(seed=0, count=64)
+    dofs = sum(w.kinetic_dofs for w in mix)
+    stream = torch.cuda.Stream()
+    ctxs = []
+    for w in mix:
+        c = kin.Context.from_workload(w, precision=kin.KIN_FP32, torch_alloc=True, stream=stream.cuda_stream)
+        c.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+        ctxs.append(c)
+    batch = kin.Batch(ctxs, stream=stream.cuda_stream)
+    batch.step(args.warmup)
+    batch.sync()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        el = _events_time(stream, lambda: batch.step(1), args.steps)
+        clk.mark(t0, time.perf_counter())
+    batch.sync()
+    value = dofs * args.steps / el
+    launches_per_step = len({(c.info.degree, c.info.specialised) for c in ctxs})
+    batch.close()
+    for c in ctxs:
+        c.close()
+    # plain FP64 path: the same instances one at a time
+    ctx64 = []
+    for w in mix:
+        c = kin.Context.from_workload(w, precision=kin.KIN_FP64, torch_alloc=True, stream=stream.cuda_stream)
+        c.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+        ctx64.append(c)
+    k64 = max(1, min(args.steps, 5))
+
+    def one_at_a_time():
+        for c in ctx64:
+            c.step(1)
+    one_at_a_time()
+    stream.synchronize()
+    el64 = _events_time(stream, one_at_a_time, k64)
+    value64 = dofs * k64 / el64
+    for c in ctx64:
+        c.close()
+    peak, peak_kind = measured_peak_hbm()
+    ms = 1e3 * el / args.steps
+    achieved = 8 * dofs / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched-64x-euler2d-D2Q4-n64..512-p1..3-32cell-subdomains-K3",
+                   "instances": len(mix), "kinetic_dofs": dofs, "state_bytes": 4 * dofs,
+                   "l2": "state 3.4 GB exceeds L2; no flush", "launches_per_step": launches_per_step},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind},
+        "plain_fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * el64 / k64,
+                       "path": "each instance stepped alone, FP64"},
+        "batched_over_plain_fp64": value / value64,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Seeded Poisson stream (200 requests/s) of 2D Euler / D2Q4 requests, mesh
+    64^2..1024^2 (log-uniform over powers of two), degree 1..3, 50..500
+    steps, FP32 state resident on the device, admitted under a 150 GB budget;
+    continuous batching (paper_2212_11010_gb300.serve)."""
+    import torch
+    import workloads
+    import paper_2212_11010_gb300 as kin
+    from paper_2212_11010_gb300 import build as kbuild
+    from paper_2212_11010_gb300 import serve
+    torch.cuda.set_device(0)
+    if not kbuild.up_to_date():
+        kbuild.build()
+    kin.load_library()
+    reqs = workloads.serving_stream(seed=0, count=args.requests, rate=200.0)
+    for r in reqs:
+        r.seed = 0            # one initial field per (kind, n, degree): client data, prepared up front
+    for r in reqs:
+        workloads.request_workload(r)
+    # warm-up: one small request through the server (module load, graph set-up paths)
+    warm = workloads.serving_stream(seed=9, count=2, rate=1000.0, sizes=(64,), steps=(5, 5))
+    serve.Server(budget_bytes=150e9).run(warm, workloads.request_workload)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        recs = serve.Server(budget_bytes=150e9, chunk_steps=25, keep_results=False).run(
+            reqs, workloads.request_workload)
+        clk.mark(t0, time.perf_counter())
+    st = serve.summarize(recs)
+    line = {
+        "metric": METRIC, "value": st["dof_updates_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": None, "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving-poisson200-euler2d-D2Q4-n64..1024-p1..3-steps50..500",
+                   "requests": st["requests"], "hbm_budget_bytes": 150e9, "chunk_steps": 25},
+        "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+                    "makespan_s": st["makespan_s"],
+                    "note": "offered load exceeds the device's throughput; latency includes queueing"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,12 +476,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="vortex2d",
-                    choices=["vortex2d", "densitywave3d", "advection1d"])
+                    choices=["vortex2d", "densitywave3d", "advection1d", "batched", "serving"])
+    ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

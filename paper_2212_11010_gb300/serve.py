@@ -1,0 +1,125 @@
+"""Continuous-batching request loop over the C ABI.
+
+Requests (one kinetic DG simulation each: mesh, degree, step count) arrive
+over time.  The server keeps every admitted request's kinetic state resident
+on the device, admits arrivals in order as long as the device-memory budget
+allows, and advances all active requests together: each round is one
+kin_batch_step over the active set (one launch per kernel type per step),
+after which finished requests are read back and retired and newly arrived
+ones join.  Latency of a request = completion time - arrival time.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import KIN_FP32, Batch, Context
+
+
+@dataclass
+class Served:
+    rid: int
+    arrival: float
+    admitted: float = None
+    finished: float = None
+    steps: int = 0
+    dofs: int = 0
+    result: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+def state_bytes_estimate(w, esize=4) -> int:
+    """Conservative device bytes of a request before its context exists:
+    kinetic state, block summaries (at most half of it) and FP64 staging."""
+    f = w.kinetic_dofs * esize
+    return int(f * 1.5 + w.m * w.nodes * 8 + (1 << 20))
+
+
+class Server:
+    def __init__(self, budget_bytes: float = 150e9, chunk_steps: int = 25, torch_alloc: bool = True,
+                 keep_results: bool = True):
+        self.budget = float(budget_bytes)
+        self.chunk = int(chunk_steps)
+        self.torch_alloc = torch_alloc
+        self.keep_results = keep_results
+
+    def run(self, requests, workload_of, clock=time.perf_counter):
+        """requests: objects with rid, arrival (s), steps; workload_of(r) -> Workload.
+        Returns the Served records in request order."""
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        records = {r.rid: Served(r.rid, r.arrival) for r in requests}
+        active = []            # (record, context, remaining steps, bytes)
+        used = 0.0
+        batch = None
+        dirty = False
+        t0 = clock()
+        while pending or active:
+            now = clock() - t0
+            while pending and pending[0].arrival <= now:
+                r = pending[0]
+                w = workload_of(r)
+                need = state_bytes_estimate(w)
+                if used + need > self.budget and active:
+                    break                                  # wait for memory to free up
+                pending.popleft()
+                ctx = Context.from_workload(w, precision=KIN_FP32, torch_alloc=self.torch_alloc)
+                ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+                rec = records[r.rid]
+                rec.admitted = clock() - t0
+                rec.steps = r.steps
+                rec.dofs = w.kinetic_dofs
+                used += ctx.info.device_bytes
+                active.append([rec, ctx, r.steps, ctx.info.device_bytes])
+                dirty = True
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
+                continue
+            if dirty:
+                if batch is not None:
+                    batch.close()
+                batch = Batch([a[1] for a in active])
+                dirty = False
+            k = min(self.chunk, min(a[2] for a in active))
+            batch.step(k)
+            batch.sync()
+            still = []
+            for a in active:
+                a[2] -= k
+                if a[2] == 0:
+                    rec, ctx = a[0], a[1]
+                    W = ctx.get_state()
+                    rec.finished = clock() - t0
+                    if self.keep_results:
+                        rec.result = W
+                    used -= a[3]
+                    dirty = True
+                else:
+                    still.append(a)
+            if dirty and batch is not None:
+                batch.close()
+                batch = None
+            for a in active:
+                if a[2] == 0:
+                    a[1].close()
+            active = still
+        if batch is not None:
+            batch.close()
+        return [records[r.rid] for r in requests]
+
+
+def summarize(records):
+    lat = np.array([r.latency for r in records])
+    t_first = min(r.arrival for r in records)
+    t_last = max(r.finished for r in records)
+    work = sum(r.dofs * r.steps for r in records)
+    return {"requests": len(records), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "makespan_s": t_last - t_first, "dof_updates": work,
+            "dof_updates_per_s": work / (t_last - t_first)}

@@ -253,3 +253,53 @@ def batched_mix(seed: int = 0, count: int = 64, sizes=(64, 128, 256, 512), degre
             w = densitywave2d(seed=sub_seed, n=n, degree=p, tiles=tiles, dt_mult=mult, steps=steps)
         out.append(w)
     return out
+
+
+@dataclass
+class Request:
+    """One simulation request of a serving stream."""
+    rid: int
+    arrival: float        # seconds after the start of the stream
+    kind: str             # "vortex" or "densitywave"
+    n: int
+    degree: int
+    steps: int
+    seed: int
+
+
+def serving_stream(seed: int = 0, count: int = 64, rate: float = 200.0, sizes=(64, 128, 256, 512, 1024),
+                   degrees=(1, 2, 3), steps=(50, 500)):
+    """Poisson arrivals (mean 'rate' per second) of 2D Euler / D2Q4 requests:
+    mesh n x n with n log-uniform over the powers of two in [64, 1024]
+    (uniform over the exponents), DG degree uniform in 'degrees', step count
+    uniform in [steps[0], steps[1]], vortex or density wave 50/50."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        out.append(Request(i, t, "vortex" if rng.uniform() < 0.5 else "densitywave",
+                           int(rng.choice(sizes)), int(rng.choice(degrees)),
+                           int(rng.integers(steps[0], steps[1] + 1)), int(rng.integers(0, 8))))
+    return out
+
+
+_request_cache = {}
+
+
+def request_workload(r: Request, cache: bool = True) -> Workload:
+    """The problem of a request (dt = 5 x the explicit DG limit, 32-cell
+    subdomains, FP32).  Initial data of equal (kind, n, degree, seed) are
+    generated once and shared."""
+    key = (r.kind, r.n, r.degree, r.seed)
+    if cache and key in _request_cache:
+        w = _request_cache[key]
+    else:
+        tiles = max(1, r.n // 32)
+        if r.kind == "vortex":
+            w = vortex2d(seed=r.seed, n=r.n, degree=r.degree, tiles=tiles)
+        else:
+            w = densitywave2d(seed=r.seed, n=r.n, degree=r.degree, tiles=tiles)
+        if cache:
+            _request_cache[key] = w
+    return replace(w, steps=r.steps)
