@@ -108,6 +108,11 @@ __device__ __forceinline__ const float* coef_rec<float>(const Inst& I, int dir) 
 template <>
 __device__ __forceinline__ const double* coef_rec<double>(const Inst& I, int dir) { return I.cd[dir]; }
 
+// One coefficient by direct member access (constant-bank operand when the
+// indices are compile-time and I is the kernel parameter).
+__device__ __forceinline__ float coef_of(const Inst& I, int dir, int k, float) { return I.cf[dir][k]; }
+__device__ __forceinline__ double coef_of(const Inst& I, int dir, int k, double) { return I.cd[dir][k]; }
+
 // Inflow of the final subdomain iterate for the line 'gline' of population
 // 'pop' (axis a, sign sgn) entering block 'bidx' (see the header comment): the
 // raw outflow value of subdomain S-K, then in downwind order the blocks of the
@@ -123,16 +128,19 @@ __device__ __forceinline__ T chain_inflow(const Inst& I, int a, int sgn, int bid
     const long long gl = I.ax[a].glines;
     const T* __restrict__ sig = static_cast<const T*>(I.sig_in) + (long long)pop * I.sig_stride + gline;
     const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)pop * I.raw_stride + gline;
-    const T RB = coef_rec<T>(I, 2 * a + sgn)[kOffRhoB];
+    const T RB = coef_of(I, 2 * a + sgn, kOffRhoB, T(0));
     int s0 = S - K;
     while (s0 < 0) s0 += NS;
     T t = __ldg(raw + (long long)s0 * gl);
     const int cnt = (K - 1) * nb + r;
-    int qq = (s0 + 1 == NS) ? 0 : (s0 + 1) * nb;
+    // walk the summaries of blocks q0, q0+1, ... (periodic) by pointer stride
+    const T* p = sig + (long long)((s0 + 1 == NS) ? 0 : (s0 + 1) * nb) * gl;
+    const T* const end = sig + (long long)nbk * gl;
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
-        t = fma(RB, t, __ldg(sig + (long long)qq * gl));
-        qq = (qq + 1 == nbk) ? 0 : qq + 1;
+        t = fma(RB, t, __ldg(p));
+        p += gl;
+        if (p == end) p = sig;
     }
     return t;
 }

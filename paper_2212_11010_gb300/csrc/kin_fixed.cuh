@@ -174,7 +174,7 @@ __device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, in
     constexpr int BA = S::ext(A);
     constexpr int CST = S::cstep(S::RP, A);
     constexpr int NS = S::nstep(A);
-    const T* rec = coef_rec<T>(I, 2 * A + SGN);
+    constexpr int DIR = 2 * A + SGN;
 
     if (MODE == 0) {
         // look-back inflows (before the tile's data has arrived)
@@ -190,9 +190,9 @@ __device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, in
         T Pm[NP][NP], g[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            g[i] = rec[kOffG + i];
+            g[i] = coef_of(I, DIR, kOffG + i, T(0));
 #pragma unroll
-            for (int j = 0; j < NP; ++j) Pm[i][j] = rec[i * NP + j];
+            for (int j = 0; j < NP; ++j) Pm[i][j] = coef_of(I, DIR, i * NP + j, T(0));
         }
 #pragma unroll
         for (int k = 0; k < KPT; ++k) {
@@ -223,8 +223,8 @@ __device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, in
     } else {
         T prow[NP];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) prow[j] = rec[kOffProw + j];
-        const T rho = rec[kOffRho];
+        for (int j = 0; j < NP; ++j) prow[j] = coef_of(I, DIR, kOffProw + j, T(0));
+        const T rho = coef_of(I, DIR, kOffRho, T(0));
 #pragma unroll
         for (int k = 0; k < KPT; ++k) {
             const int it = hid + k * HALF;

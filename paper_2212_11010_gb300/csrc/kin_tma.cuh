@@ -81,11 +81,16 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned pari
 }
 
 // Wait for phase 'parity' of the barrier for at most 'cycles' SM clocks.
+// Between polls the thread sleeps (__nanosleep, growing to 256 ns), so a
+// waiting warp issues almost nothing while the bulk copies are in flight.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long cycles)
 {
     const long long t0 = clock64();
-    while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
+    unsigned ns = 32;
+    while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > cycles) return false;
+        __nanosleep(ns);
+        if (ns < 256) ns *= 2;
     }
     return true;
 }
