@@ -26,6 +26,8 @@ _LIB = os.path.join(_HERE, "libkin_oracle.so")
 
 ADVECTION = 0
 EULER = 1
+AXIS = 0        # 2d velocities +-lambda e_a (D1Q2, D2Q4, D3Q6)
+SIMPLEX = 1     # d + 1 velocities (D1Q2, D2Q3, D3Q4)
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +63,7 @@ class _Problem(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("tiles", ctypes.c_int * 3),
         ("iters", ctypes.c_int),
+        ("velset", ctypes.c_int),
     ]
 
 
@@ -78,6 +81,7 @@ def lib():
             "ko_num_vars": ([pp], ctypes.c_int),
             "ko_num_vel": ([pp], ctypes.c_int),
             "ko_num_nodes": ([pp], ctypes.c_size_t),
+            "ko_velocity": ([pp, ctypes.c_int, dp], ctypes.c_int),
             "ko_gll": ([ctypes.c_int, dp, dp], ctypes.c_int),
             "ko_diff_matrix": ([ctypes.c_int, dp], ctypes.c_int),
             "ko_node_coords": ([pp, dp], ctypes.c_int),
@@ -124,6 +128,7 @@ class Problem:
     adv: tuple = (1.0, 0.0, 0.0)
     tiles: tuple = (1, 1, 1)
     iters: int = 3
+    velset: int = AXIS
     _c: _Problem = field(default=None, repr=False, compare=False)
 
     def c(self) -> _Problem:
@@ -144,6 +149,7 @@ class Problem:
         p.dt = self.dt
         p.tiles = (ctypes.c_int * 3)(*pad(self.tiles, 1))
         p.iters = self.iters
+        p.velset = self.velset
         self._c = p
         return p
 
@@ -153,7 +159,7 @@ class Problem:
 
     @property
     def nvel(self) -> int:
-        return 2 * self.dim
+        return lib().ko_num_vel(ctypes.byref(self.c()))
 
     @property
     def npop(self) -> int:
@@ -162,6 +168,12 @@ class Problem:
     @property
     def nodes(self) -> int:
         return int(lib().ko_num_nodes(ctypes.byref(self.c())))
+
+
+def velocity(P: Problem, k: int) -> np.ndarray:
+    V = np.zeros(3)
+    _check(lib().ko_velocity(ctypes.byref(P.c()), k, _dp(V)), "velocity")
+    return V[:P.dim]
 
 
 def gll(p: int):

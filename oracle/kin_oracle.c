@@ -69,11 +69,15 @@ static int check_problem(const ko_problem* P)
     }
     if (!(P->lambda > 0) || !(P->dt > 0)) return -8;
     if (P->iters < 0) return -9;
+    if (P->velset != KO_AXIS && P->velset != KO_SIMPLEX) return -10;
     return 0;
 }
 
 int ko_num_vars(const ko_problem* P) { return P->system == KO_EULER ? P->dim + 2 : 1; }
-int ko_num_vel(const ko_problem* P) { return 2 * P->dim; }
+int ko_num_vel(const ko_problem* P)
+{
+    return (P->velset == KO_SIMPLEX && P->dim > 1) ? P->dim + 1 : 2 * P->dim;
+}
 
 static int nodes_per_axis(const ko_problem* P, int a) { return a < P->dim ? P->degree + 1 : 1; }
 
@@ -226,26 +230,68 @@ int ko_flux(const ko_problem* P, const double* W, int axis, double* Q)
     return 0;
 }
 
-/* M_{k=2a+s}(W) = W/(2d) + (s ? -1 : +1) Q^a(W)/(2 lambda): sum_k M_k = W and
- * sum_k V_k^a M_k = lambda (M_{2a} - M_{2a+1}) = Q^a, eq. maxwell_def. */
-int ko_maxwellian(const ko_problem* P, const double* W, double* M)
-{
-    int m = ko_num_vars(P), d = P->dim;
-    double Q[8];
-    for (int a = 0; a < d; ++a) {
-        ko_flux(P, W, a, Q);
-        for (int v = 0; v < m; ++v) {
-            M[(2 * a) * m + v] = W[v] / (2.0 * d) + Q[v] / (2.0 * P->lambda);
-            M[(2 * a + 1) * m + v] = W[v] / (2.0 * d) - Q[v] / (2.0 * P->lambda);
-        }
-    }
-    return 0;
-}
-
 static void velocity(const ko_problem* P, int k, double V[3])
 {
     V[0] = V[1] = V[2] = 0.0;
+    if (P->velset == KO_SIMPLEX && P->dim == 2) {
+        /* D2Q3, Sec. 2.4: V_k = lambda (cos(2 k pi / 3), sin(2 k pi / 3)) */
+        V[0] = P->lambda * cos(2.0 * M_PI * k / 3.0);
+        V[1] = P->lambda * sin(2.0 * M_PI * k / 3.0);
+        return;
+    }
+    if (P->velset == KO_SIMPLEX && P->dim == 3) {
+        /* D3Q4, Sec. 6.1.3: (l,l,l), (l,-l,-l), (-l,l,-l), (-l,-l,l) */
+        static const double s[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+        for (int a = 0; a < 3; ++a) V[a] = P->lambda * s[k][a];
+        return;
+    }
     V[k / 2] = (k % 2 == 0) ? P->lambda : -P->lambda;
+}
+
+int ko_velocity(const ko_problem* P, int k, double* V)
+{
+    if (check_problem(P) || k < 0 || k >= ko_num_vel(P) || !V) return -1;
+    velocity(P, k, V);
+    return 0;
+}
+
+static int lu_factor(int n, double* A, int* piv);
+static void lu_solve(int n, const double* LU, const int* piv, double* b);
+
+/* Axis sets: M_{k=2a+s}(W) = W/(2d) + (s ? -1 : +1) Q^a(W)/(2 lambda), so that
+ * sum_k M_k = W and sum_k V_k^a M_k = lambda (M_{2a} - M_{2a+1}) = Q^a.
+ * Simplex sets: eq. maxwell_def is a square system for the d + 1 unknowns of
+ * every variable, rows (sum_k M_k, sum_k V_k^1 M_k, ..., sum_k V_k^d M_k)
+ * = (W, Q^1, ..., Q^d); it is solved here by LU. */
+int ko_maxwellian(const ko_problem* P, const double* W, double* M)
+{
+    int m = ko_num_vars(P), d = P->dim, nv = ko_num_vel(P);
+    double Q[3][8];
+    for (int a = 0; a < d; ++a) ko_flux(P, W, a, Q[a]);
+    if (nv == 2 * d) {
+        for (int a = 0; a < d; ++a)
+            for (int v = 0; v < m; ++v) {
+                M[(2 * a) * m + v] = W[v] / (2.0 * d) + Q[a][v] / (2.0 * P->lambda);
+                M[(2 * a + 1) * m + v] = W[v] / (2.0 * d) - Q[a][v] / (2.0 * P->lambda);
+            }
+        return 0;
+    }
+    double A[16], V[3];
+    int piv[4];
+    for (int k = 0; k < nv; ++k) {
+        velocity(P, k, V);
+        A[0 * nv + k] = 1.0;
+        for (int a = 0; a < d; ++a) A[(1 + a) * nv + k] = V[a];
+    }
+    if (lu_factor(nv, A, piv)) return -2;
+    for (int v = 0; v < m; ++v) {
+        double b[4];
+        b[0] = W[v];
+        for (int a = 0; a < d; ++a) b[1 + a] = Q[a][v];
+        lu_solve(nv, A, piv, b);
+        for (int k = 0; k < nv; ++k) M[k * m + v] = b[k];
+    }
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */

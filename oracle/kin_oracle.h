@@ -10,8 +10,12 @@
  *
  * Conventions (identical on both sides, but written separately):
  *   d        space dimension (1..3), m conserved variables.
- *   k        kinetic velocity index, k = 2*a + s: V_k = +lambda e_a (s = 0)
- *            or -lambda e_a (s = 1)  (D1Q2, D2Q4, D3Q6 sets).
+ *   k        kinetic velocity index.  Axis sets (velset KO_AXIS; D1Q2, D2Q4,
+ *            D3Q6): k = 2*a + s, V_k = +lambda e_a (s = 0) or -lambda e_a
+ *            (s = 1).  Simplex sets (velset KO_SIMPLEX; d + 1 velocities,
+ *            Sec. 2.1): D1Q2 as above, D2Q3 V_k = lambda (cos 2k pi/3,
+ *            sin 2k pi/3) (Sec. 2.4), D3Q4 the cube diagonals with components
+ *            +-lambda (Sec. 6.1.3).
  *   pop      population index pop = k*m + v  (velocity-major).
  *   Storage  W[v][cz][cy][cx][nz][ny][nx] and f[pop][cz][cy][cx][nz][ny][nx]:
  *            cells row-major with x fastest, then the (p+1)^d tensor GLL
@@ -29,6 +33,7 @@ extern "C" {
 #endif
 
 enum { KO_ADVECTION = 0, KO_EULER = 1 };
+enum { KO_AXIS = 0, KO_SIMPLEX = 1 };
 
 typedef struct {
     int dim;            /* d, 1..3                                            */
@@ -44,10 +49,13 @@ typedef struct {
     double dt;          /* time step                                          */
     int tiles[3];       /* subdomains per axis; must divide n[a]              */
     int iters;          /* subdomain iterations K (>= 1); 0 = to fixed point  */
+    int velset;         /* KO_AXIS (2d velocities) or KO_SIMPLEX (d + 1)      */
 } ko_problem;
 
 int    ko_num_vars(const ko_problem* P);          /* m                      */
-int    ko_num_vel(const ko_problem* P);           /* 2d                     */
+int    ko_num_vel(const ko_problem* P);           /* 2d or d + 1            */
+/* V_k (3 components, unused ones 0). */
+int    ko_velocity(const ko_problem* P, int k, double* V);
 size_t ko_num_nodes(const ko_problem* P);         /* cells * (p+1)^d        */
 
 /* GLL nodes on [0,1] and weights summing to 1 (Sec. 3.1 basis; Gauss-Lobatto
@@ -59,7 +67,8 @@ int ko_diff_matrix(int p, double* D);
 int ko_node_coords(const ko_problem* P, double* xyz);
 
 /* Physical flux Q^a(W) (eq. conslaw) and the Maxwellians M_k(W) of all
- * velocities at one point (eq. maxwell_def with the 2d-velocity reading). */
+ * velocities at one point: eq. maxwell_def solved as a linear system for the
+ * d + 1 simplex velocities, and the 2d-velocity reading for axis sets. */
 int ko_flux(const ko_problem* P, const double* W, int axis, double* Q);
 int ko_maxwellian(const ko_problem* P, const double* W, double* M);
 

@@ -1,0 +1,37 @@
+"""The autotuner changes only the schedule: the schedule it picks gives the
+same result as the default one (up to FP32 round-off) and is cached."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kin():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_11010_gb300 import build
+    build.build()
+    import paper_2212_11010_gb300 as kin
+    kin.load_library()
+    return kin
+
+
+def test_tuned_schedule_same_result(kin, tmp_path):
+    from paper_2212_11010_gb300 import autotune
+    w = workloads.with_(workloads.vortex2d(seed=2, n=64, degree=2, tiles=2), tiles=(2, 2))
+    best, timings = autotune.tune(w, steps=3, cache_file=str(tmp_path / "tune.json"))
+    assert len(timings) >= 5 and best in timings
+    assert timings[best] == min(timings.values())
+    again, t2 = autotune.tune(w, cache_file=str(tmp_path / "tune.json"))
+    assert again == best and t2 == {}
+    outs = []
+    for kw in ({}, best.kwargs()):
+        with kin.Context.from_workload(w, **kw) as ctx:
+            ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+            ctx.step(5)
+            outs.append(ctx.get_state())
+    assert np.abs(outs[0] - outs[1]).max() / np.abs(outs[0]).max() < 1e-6

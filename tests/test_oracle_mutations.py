@@ -24,8 +24,8 @@ MUTATIONS = {
     "interior_uses_previous_iterate": ("const double* src = boundary ? prev : cur;",
                                        "const double* src = prev;"),
     "crank_nicolson_extrapolation_dropped": ("f[i] = 2.0 * cur[i] - f[i];", "f[i] = cur[i];"),
-    "maxwellian_flux_sign": ("M[(2 * a) * m + v] = W[v] / (2.0 * d) + Q[v] / (2.0 * P->lambda);",
-                             "M[(2 * a) * m + v] = W[v] / (2.0 * d) - Q[v] / (2.0 * P->lambda);"),
+    "maxwellian_flux_sign": ("M[(2 * a) * m + v] = W[v] / (2.0 * d) + Q[a][v] / (2.0 * P->lambda);",
+                             "M[(2 * a) * m + v] = W[v] / (2.0 * d) - Q[a][v] / (2.0 * P->lambda);"),
     "pressure_dropped": ("Q[1 + b] = W[1 + b] * ua + (b == axis ? pr : 0.0);",
                          "Q[1 + b] = W[1 + b] * ua;"),
     "relaxation_sign": ("*fp = P->omega * M[pop] + (1.0 - P->omega) * (*fp);",
@@ -38,10 +38,16 @@ MUTATIONS = {
     "gll_weight_power": ("w[j] = 0.5 * 2.0 / (p * (p + 1.0) * pp * pp);",
                          "w[j] = 0.5 * 2.0 / (p * (p + 1.0) * pp);"),
     "sweep_direction": ("if (C->V[a] < 0) {", "if (C->V[a] > 0) {"),
+    "d2q3_angle": ("V[0] = P->lambda * cos(2.0 * M_PI * k / 3.0);",
+                   "V[0] = P->lambda * cos(2.0 * M_PI * k / 4.0);"),
+    "d3q4_diagonal_sign": ("{{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}}",
+                           "{{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, -1}}"),
+    "moment_row_velocity_component": ("for (int a = 0; a < d; ++a) A[(1 + a) * nv + k] = V[a];",
+                                      "for (int a = 0; a < d; ++a) A[(1 + a) * nv + k] = V[d - 1 - a];"),
 }
 
 PIN_FILES = ["tests/test_oracle_basis.py", "tests/test_oracle_relaxation.py",
-             "tests/test_oracle_transport.py"]
+             "tests/test_oracle_transport.py", "tests/test_oracle_simplex.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))

@@ -68,14 +68,19 @@ class Workload:
     precision: str            # "f64" or "f32"
     W0: np.ndarray = field(repr=False)
     exact: Optional[Callable] = field(default=None, repr=False)  # exact(t) -> W
+    velset: int = 0           # 0: 2d velocities +-lambda e_a; 1: d + 1 velocities (D2Q3, D3Q4)
 
     @property
     def m(self) -> int:
         return 1 if self.system == ADVECTION else self.dim + 2
 
     @property
+    def nvel(self) -> int:
+        return self.dim + 1 if (self.velset == 1 and self.dim > 1) else 2 * self.dim
+
+    @property
     def npop(self) -> int:
-        return 2 * self.dim * self.m
+        return self.nvel * self.m
 
     @property
     def nodes(self) -> int:
@@ -88,7 +93,8 @@ class Workload:
     def oracle_kwargs(self) -> dict:
         return dict(dim=self.dim, n=self.n, lo=self.lo, hi=self.hi, degree=self.degree,
                     system=self.system, lam=self.lam, dt=self.dt, omega=self.omega,
-                    gamma=self.gamma, adv=self.adv, tiles=self.tiles, iters=self.iters)
+                    gamma=self.gamma, adv=self.adv, tiles=self.tiles, iters=self.iters,
+                    velset=self.velset)
 
 
 def node_coords(dim, n, lo, hi, degree) -> np.ndarray:
@@ -188,7 +194,14 @@ def vortex2d(seed: int = 0, n: int = 256, degree: int = 2, tiles: int = 8, iters
                     gamma, (0.0, 0.0, 0.0), _tiles(tiles, 2), iters, steps, precision, W0, exact)
 
 
-def _densitywave(dim, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision, amp=0.2):
+# Kinetic speed factor for the d + 1 velocity sets (lambda = factor * a_max):
+# D2Q3 (|V_k| = lambda) and D3Q4 (components +-lambda); chosen with margin
+# above the stability limit observed on the density wave.
+SIMPLEX_LAMBDA = {2: 2.0, 3: 1.5}
+
+
+def _densitywave(dim, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision, amp=0.2,
+                 velset=0):
     rng = np.random.default_rng(seed)
     phi = rng.uniform(0.0, 2 * np.pi)
     gamma = 1.4
@@ -205,7 +218,7 @@ def _densitywave(dim, seed, n, degree, tiles, iters, dt_mult, omega, steps, prec
 
     rho, vel, pr = fields(0.0)
     amax = _max_speed(rho, vel, pr, gamma)
-    lam = 1.1 * dim * amax
+    lam = (SIMPLEX_LAMBDA[dim] if velset == 1 else 1.1 * dim) * amax
     h = 1.0 / n
     dt = dt_mult * h / ((2 * degree + 1) * dim * amax)
 
@@ -215,19 +228,21 @@ def _densitywave(dim, seed, n, degree, tiles, iters, dt_mult, omega, steps, prec
 
     return Workload(f"densitywave{dim}d", dim, (n,) * dim, lo, hi, degree, EULER, lam, dt, omega,
                     gamma, (0.0, 0.0, 0.0), _tiles(tiles, dim), iters, steps, precision,
-                    _euler_conserved(rho, vel, pr, gamma), exact)
+                    _euler_conserved(rho, vel, pr, gamma), exact, velset)
 
 
 def densitywave3d(seed: int = 0, n: int = 128, degree: int = 1, tiles: int = 16, iters: int = 3,
                   dt_mult: float = 5.0, omega: float = 2.0, steps: int = 200,
-                  precision: str = "f32") -> Workload:
-    return _densitywave(3, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision)
+                  precision: str = "f32", velset: int = 0) -> Workload:
+    return _densitywave(3, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision,
+                        velset=velset)
 
 
 def densitywave2d(seed: int = 0, n: int = 64, degree: int = 1, tiles: int = 2, iters: int = 3,
                   dt_mult: float = 5.0, omega: float = 2.0, steps: int = 100,
-                  precision: str = "f32") -> Workload:
-    return _densitywave(2, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision)
+                  precision: str = "f32", velset: int = 0) -> Workload:
+    return _densitywave(2, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision,
+                        velset=velset)
 
 
 def with_(w: Workload, **kw) -> Workload:
