@@ -52,6 +52,12 @@ def make_workload(name):
     elif name == "advection1d":
         w = workloads.advection1d(seed=0, n=256, tiles=4)
         desc = "advection1d-256-p1-D1Q2-4sub-K3"
+    elif name == "vortex2d-d2q3":
+        w = workloads.vortex2d(seed=0, velset=1)
+        desc = "vortex2d-euler-256x256-p2-D2Q3-8x8sub-K3"
+    elif name == "densitywave3d-d3q4":
+        w = workloads.densitywave3d(seed=0, velset=1)
+        desc = "densitywave3d-euler-128^3-p1-D3Q4-16^3sub-K3"
     else:
         raise SystemExit(f"unknown workload {name}")
     return w, desc
@@ -476,7 +482,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="vortex2d",
-                    choices=["vortex2d", "densitywave3d", "advection1d", "batched", "serving"])
+                    choices=["vortex2d", "densitywave3d", "advection1d", "batched", "serving",
+                             "vortex2d-d2q3", "densitywave3d-d3q4"])
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -57,7 +57,15 @@ typedef enum {
 } kin_status;
 
 enum { KIN_ADVECTION = 0, KIN_EULER = 1 };          /* kin_model.system   */
-enum { KIN_D1Q2 = 1, KIN_D2Q4 = 2, KIN_D3Q6 = 3 };  /* kin_model.velset   */
+/* kin_model.velset: 2d axis velocities +-lambda e_a (D1Q2, D2Q4, D3Q6; the
+ * value is the dimension), or the paper's d + 1 sets: D2Q3 with
+ * V_k = lambda (cos 2k pi/3, sin 2k pi/3) (Sec. 2.4) and D3Q4 with the cube
+ * diagonals (+-lambda, +-lambda, +-lambda) (Sec. 6.1.3), whose Maxwellians
+ * solve eq. maxwell_def exactly.  The d + 1 sets are transported by K
+ * literal subdomain iterations with wavefront sweeps (one subdomain of one
+ * population in shared memory, so a subdomain may hold at most 227 KB of
+ * one population); kin_diag's next_defect is not available for them. */
+enum { KIN_D1Q2 = 1, KIN_D2Q4 = 2, KIN_D3Q6 = 3, KIN_D2Q3 = 4, KIN_D3Q4 = 5 };
 enum { KIN_FP64 = 0, KIN_FP32 = 1 };                /* kin_opts.precision */
 
 /* Periodic Cartesian box [lo, hi] with n[a] cells along axis a (axes >= dim

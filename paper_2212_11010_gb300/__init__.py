@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libkin.so")
 
 KIN_OK, KIN_EINVAL, KIN_ENOMEM, KIN_EBUDGET, KIN_ECUDA, KIN_ETIMEOUT, KIN_ESTATE = range(7)
 KIN_ADVECTION, KIN_EULER = 0, 1
-KIN_D1Q2, KIN_D2Q4, KIN_D3Q6 = 1, 2, 3
+KIN_D1Q2, KIN_D2Q4, KIN_D3Q6, KIN_D2Q3, KIN_D3Q4 = 1, 2, 3, 4, 5
 KIN_FP64, KIN_FP32 = 0, 1
 KIN_DEBUG_STALL_LOAD = 1
 
@@ -280,11 +280,13 @@ def kin_last_error(ctx=None) -> str:
 
 def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 0.0),
               tiles=(1, 1, 1), iters=3, precision=KIN_FP64, block=(0, 0, 0), mem_budget=0,
-              stream=None, torch_alloc=False, wait_timeout_s=0.0, debug_flags=0, threads=0, stages=0):
+              stream=None, torch_alloc=False, wait_timeout_s=0.0, debug_flags=0, threads=0, stages=0,
+              velset=None):
     pad = lambda t, fill: tuple(t) + (fill,) * (3 - len(tuple(t)))
     mesh = kin_mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
                     (ctypes.c_double * 3)(*pad(hi, 1.0)))
-    model = kin_model(system, dim, lam, gamma, (ctypes.c_double * 3)(*pad(adv, 0.0)), omega)
+    model = kin_model(system, dim if velset is None else velset, lam, gamma,
+                      (ctypes.c_double * 3)(*pad(adv, 0.0)), omega)
     opts = kin_opts()
     opts.tiles = (ctypes.c_int * 3)(*pad(tiles, 1))
     opts.iters = iters
@@ -346,8 +348,9 @@ class Context:
     @classmethod
     def from_workload(cls, w, precision=None, **kw):
         prec = precision if precision is not None else (KIN_FP32 if w.precision == "f32" else KIN_FP64)
+        vs = {2: KIN_D2Q3, 3: KIN_D3Q4}.get(w.dim) if getattr(w, "velset", 0) == 1 else None
         return cls(w.dim, w.n, w.lo, w.hi, w.degree, w.system, w.lam, w.dt, omega=w.omega,
-                   gamma=w.gamma, adv=w.adv, tiles=w.tiles, iters=w.iters, precision=prec, **kw)
+                   gamma=w.gamma, adv=w.adv, tiles=w.tiles, iters=w.iters, precision=prec, velset=vs, **kw)
 
     @property
     def dtype(self):

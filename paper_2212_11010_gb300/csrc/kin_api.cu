@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -50,6 +51,16 @@ struct kin_ctx {
     int smem = 0, grid = 0, stages = 1, threads = kThreads;
     int want_threads = 0, want_stages = 0;
     bool fixed = false;                    // compile-time block shape kernel in use
+    // d + 1 velocity sets
+    bool simplex = false;
+    int vsgn[4][3] = {};
+    double minv[16] = {};
+    void* sxcoef = nullptr;
+    double* sxc64 = nullptr;
+    double* sxwork = nullptr;
+    void* sxtr[2][3] = {};
+    size_t sx_smem = 0;
+    int sx_stride = 0;
     bool have_state = false;
     long long steps_done = 0;
     bool poisoned = false;
@@ -342,6 +353,7 @@ static PointArgs point_args(const kin_ctx* c)
     p.degree = c->degree;
     p.m = c->m;
     p.system = c->system;
+    p.nvel = c->nvel;
     p.nodes = (long long)c->nodes;
     p.lambda = c->lambda;
     p.gamma = c->gamma;
@@ -359,6 +371,63 @@ static kin_status check_usable(const kin_ctx* c)
     return KIN_OK;
 }
 
+// ---- d + 1 velocity sets: launch arguments and one step ----
+static SxArgs sx_args(const kin_ctx* c)
+{
+    SxArgs S;
+    memset(&S, 0, sizeof S);
+    S.f = c->f;
+    S.coef = c->sxcoef;
+    S.nodes = (long long)c->nodes;
+    long long tn = 1;
+    for (int a = 1; a < c->dim; ++a) tn *= c->NP;
+    for (int a = 0; a < 3; ++a) {
+        S.n[a] = c->n[a];
+        S.L[a] = c->L[a];
+        S.NS[a] = c->tiles[a];
+        S.glines[a] = a < c->dim ? (long long)(c->cells / c->n[a]) * tn : 0;
+        S.adv[a] = c->adv[a];
+    }
+    for (int k = 0; k < 4; ++k)
+        for (int a = 0; a < 3; ++a) S.vsgn[k][a] = c->vsgn[k][a];
+    S.dim = c->dim;
+    S.degree = c->degree;
+    S.nn = c->NN;
+    S.m = c->m;
+    S.nvel = c->nvel;
+    S.npop = c->npop;
+    S.system = c->system;
+    S.coef_stride = c->sx_stride;
+    S.omega = c->omega;
+    S.gamma = c->gamma;
+    for (int i = 0; i < 16; ++i) S.minv[i] = c->minv[i];
+    long long total = 0;
+    for (int pop = 0; pop < c->npop; ++pop)
+        for (int a = 0; a < c->dim; ++a)
+            if (c->vsgn[pop / c->m][a] != 0) total += (long long)c->tiles[a] * S.glines[a];
+    S.trace_total = total;
+    return S;
+}
+
+// One step S(dt) for a d + 1 velocity set: trace pass, K sweeps, relaxation.
+static kin_status sx_step(kin_ctx* c)
+{
+    SxArgs S = sx_args(c);
+    const int prec = c->precision == KIN_FP32;
+    for (int a = 0; a < 3; ++a) S.tr_out[a] = c->sxtr[0][a];
+    KIN_CUDA(c, sx_launch_trace0(S, prec, c->stream));
+    for (int it = 1; it <= c->iters; ++it) {
+        for (int a = 0; a < 3; ++a) {
+            S.tr_in[a] = c->sxtr[(it - 1) & 1][a];
+            S.tr_out[a] = c->sxtr[it & 1][a];
+        }
+        S.final_iter = it == c->iters;
+        KIN_CUDA(c, sx_launch_sweep(S, prec, c->sx_smem, c->stream));
+    }
+    KIN_CUDA(c, sx_launch_relax(S, prec, c->stream));
+    return KIN_OK;
+}
+
 extern "C" {
 
 kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, double dt,
@@ -371,9 +440,13 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     if (degree < 1 || degree > 3) return fail(nullptr, KIN_EINVAL, "degree must be 1..3");
     if (model->system != KIN_ADVECTION && model->system != KIN_EULER)
         return fail(nullptr, KIN_EINVAL, "unknown system %d", model->system);
-    if (model->velset != mesh->dim)
-        return fail(nullptr, KIN_EINVAL, "velocity set D%dQ%d does not match dim %d",
-                    model->velset, 2 * model->velset, mesh->dim);
+    const bool simplex = (model->velset == KIN_D2Q3 && mesh->dim == 2) ||
+                         (model->velset == KIN_D3Q4 && mesh->dim == 3);
+    if (model->velset != mesh->dim && !simplex)
+        return fail(nullptr, KIN_EINVAL, "velocity set %d does not match dim %d", model->velset, mesh->dim);
+    if (simplex && (degree > (mesh->dim == 3 ? 2 : 3)))
+        return fail(nullptr, KIN_EINVAL, "the d+1 velocity sets support degree <= %d in %dD",
+                    mesh->dim == 3 ? 2 : 3, mesh->dim);
     if (!(model->lambda > 0) || !(dt > 0))
         return fail(nullptr, KIN_EINVAL, "lambda and dt must be positive");
     if (!(model->omega >= 1.0 && model->omega <= 2.0))
@@ -395,7 +468,8 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     c->degree = degree;
     c->system = model->system;
     c->m = model->system == KIN_EULER ? mesh->dim + 2 : 1;
-    c->nvel = 2 * mesh->dim;
+    c->simplex = simplex;
+    c->nvel = simplex ? mesh->dim + 1 : 2 * mesh->dim;
     c->npop = c->nvel * c->m;
     c->NP = degree + 1;
     c->NN = 1;
@@ -447,6 +521,99 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
         c->cells *= c->n[a];
     }
     c->nodes = c->cells * c->NN;
+
+    if (c->simplex) {
+        // signs of the velocity components (D2Q3: 0, 120, 240 degrees; D3Q4 diagonals)
+        static const int s2[3][3] = {{1, 0, 0}, {-1, 1, 0}, {-1, -1, 0}};
+        static const int s3[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+        for (int k = 0; k < c->nvel; ++k)
+            for (int a = 0; a < 3; ++a) c->vsgn[k][a] = c->dim == 2 ? s2[k][a] : s3[k][a];
+        size_t tn = 1;
+        for (int a = 1; a < c->dim; ++a) tn *= c->NP;
+        c->sx_stride = c->NN * c->NN + c->dim * c->NN * (int)tn;
+        c->sx_smem = ((size_t)c->L[0] * c->L[1] * c->L[2] * c->NN + c->sx_stride) * c->esize;
+        if (c->sx_smem > 227 * 1024) {
+            const size_t need = c->sx_smem;
+            delete c;
+            return fail(nullptr, KIN_EINVAL,
+                        "a subdomain of one population needs %zu bytes of shared memory (> 227 KB); use more tiles",
+                        need);
+        }
+        for (int a = 0; a < 3; ++a) {
+            c->B[a] = c->L[a];
+            c->nblk[a] = c->tiles[a];
+            c->nb[a] = 1;
+        }
+        c->grid = c->npop * c->tiles[0] * c->tiles[1] * c->tiles[2];
+        c->threads = kSxThreads;
+        c->smem = (int)c->sx_smem;
+        kin_status st;
+        void* p;
+#define ALLOC(dst, bytes)                                                 \
+    do {                                                                  \
+        st = dev_alloc(c, (bytes), &p);                                   \
+        if (st != KIN_OK) {                                               \
+            g_create_error = c->err;                                      \
+            release_all(c);                                               \
+            delete c;                                                     \
+            return st;                                                    \
+        }                                                                 \
+        dst = (decltype(dst))p;                                           \
+    } while (0)
+        ALLOC(c->f, c->nodes * c->npop * c->esize);
+        for (int i = 0; i < 2; ++i)
+            for (int a = 0; a < c->dim; ++a)
+                ALLOC(c->sxtr[i][a], (size_t)c->npop * c->tiles[a] * (c->cells / c->n[a]) * tn * c->esize);
+        ALLOC(c->sxc64, sizeof(double) * 4 * c->sx_stride);
+        ALLOC(c->sxcoef, c->esize == 4 ? sizeof(float) * 4 * c->sx_stride : 16);
+        ALLOC(c->sxwork, sizeof(double) * 4 * 2 * kSxMaxNN * kSxMaxNN);
+        ALLOC(c->c64, sizeof(double) * 6 * kCoefStride);
+        ALLOC(c->gll, sizeof(double) * 2 * kMaxNP);
+        ALLOC(c->Wbuf, sizeof(double) * c->m * c->nodes);
+        ALLOC(c->partial, sizeof(double) * kDiagBlocks * 6);
+        ALLOC(c->result, sizeof(double) * 16);
+        ALLOC(c->errword, sizeof(int) * 4);
+#undef ALLOC
+        if (c->esize == 8) c->sxcoef = c->sxc64;
+        SetupArgs sa;
+        memset(&sa, 0, sizeof sa);
+        sa.dim = c->dim;
+        sa.degree = degree;
+        sa.lambda = c->lambda;
+        sa.dt = dt;
+        for (int a = 0; a < 3; ++a) {
+            sa.h[a] = c->h[a];
+            sa.B[a] = 1;
+        }
+        sa.c64 = c->c64;
+        sa.gll = c->gll;     // Gauss-Lobatto weights for the mass diagnostic
+        SxSetupArgs xa;
+        memset(&xa, 0, sizeof xa);
+        xa.dim = c->dim;
+        xa.degree = degree;
+        xa.lambda = c->lambda;
+        xa.dt = dt;
+        for (int a = 0; a < 3; ++a) xa.h[a] = c->h[a];
+        xa.stride = c->sx_stride;
+        xa.c64 = c->sxc64;
+        xa.c32 = c->esize == 4 ? (float*)c->sxcoef : nullptr;
+        xa.minv = c->result;
+        xa.work = c->sxwork;
+        cudaError_t e = cudaMemsetAsync(c->errword, 0, sizeof(int) * 4, c->stream);
+        if (e == cudaSuccess) e = launch_setup(sa, c->stream);
+        if (e == cudaSuccess) e = sx_launch_setup(xa, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->minv, c->result, sizeof(double) * 16, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("setup failed: ") + cudaGetErrorString(e);
+            release_all(c);
+            delete c;
+            return KIN_ECUDA;
+        }
+        *out = c;
+        return KIN_OK;
+    }
 
     // cell block
     bool user_block = opts->block[0] || opts->block[1] || opts->block[2];
@@ -571,9 +738,13 @@ kin_status kin_set_state(kin_ctx* c, const double* W, size_t n_values, int on_de
                                     c->stream));
         src = c->Wbuf;
     }
-    KIN_CUDA(c, launch_init(point_args(c), src, c->f, c->precision == KIN_FP32, c->stream));
-    st = launch_step(c, 1);
-    if (st) return st;
+    if (c->simplex) {
+        KIN_CUDA(c, sx_launch_init(sx_args(c), src, c->precision == KIN_FP32, c->stream));
+    } else {
+        KIN_CUDA(c, launch_init(point_args(c), src, c->f, c->precision == KIN_FP32, c->stream));
+        st = launch_step(c, 1);
+        if (st) return st;
+    }
     c->have_state = true;
     c->steps_done = 0;
     if (!on_device) {
@@ -592,8 +763,10 @@ kin_status kin_set_kinetic(kin_ctx* c, const void* f, size_t n_values, int on_de
         return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
     KIN_CUDA(c, cudaMemcpyAsync(c->f, f, n_values * c->esize,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    st = launch_step(c, 1);
-    if (st) return st;
+    if (!c->simplex) {
+        st = launch_step(c, 1);
+        if (st) return st;
+    }
     c->have_state = true;
     if (!on_device) {
         KIN_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -609,7 +782,7 @@ kin_status kin_step(kin_ctx* c, int nsteps)
     if (nsteps < 0) return fail(c, KIN_EINVAL, "nsteps must be >= 0");
     if (!c->have_state) return fail(c, KIN_ESTATE, "no state: call kin_set_state or kin_set_kinetic first");
     for (int s = 0; s < nsteps; ++s) {
-        st = launch_step(c, 0);
+        st = c->simplex ? sx_step(c) : launch_step(c, 0);
         if (st) return st;
         c->steps_done++;
     }
@@ -665,7 +838,11 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
         KIN_CUDA(c, cudaStreamSynchronize(c->stream));
         for (int v = 0; v < c->m; ++v) mass_per_var[v] = host[v];
     }
-    if (next_defect || iter_residual) {
+    if ((next_defect || iter_residual) && c->simplex) {
+        if (next_defect)
+            for (int v = 0; v < c->m; ++v) next_defect[v] = NAN;
+        if (iter_residual) *iter_residual = NAN;
+    } else if (next_defect || iter_residual) {
         DefectArgs da;
         memset(&da, 0, sizeof da);
         da.dim = c->dim;
@@ -863,6 +1040,8 @@ extern "C" kin_status kin_batch_create(kin_ctx* const* members, int count, void*
         if (!members[i]) return batch_fail(nullptr, KIN_EINVAL, "member %d is NULL", i);
         if (members[i]->poisoned) return batch_fail(nullptr, KIN_ESTATE, "member %d is poisoned", i);
         if (!members[i]->have_state) return batch_fail(nullptr, KIN_ESTATE, "member %d has no state", i);
+        if (members[i]->simplex)
+            return batch_fail(nullptr, KIN_EINVAL, "member %d uses a d+1 velocity set (not batched)", i);
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return batch_fail(nullptr, KIN_EINVAL, "member %d repeats member %d", i, j);
     }

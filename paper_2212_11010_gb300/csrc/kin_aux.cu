@@ -191,7 +191,7 @@ template <typename T>
 __global__ void moments_kernel(PointArgs A, const T* __restrict__ f, double* __restrict__ W)
 {
     const long long nodes = A.nodes;
-    const int nv = 2 * A.dim;
+    const int nv = A.nvel;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
         for (int v = 0; v < A.m; ++v) {
@@ -232,7 +232,7 @@ __global__ void mass_kernel(PointArgs A, const T* __restrict__ f, const double* 
                             double* __restrict__ partial)
 {
     const long long nodes = A.nodes;
-    const int np = A.degree + 1, nv = 2 * A.dim;
+    const int np = A.degree + 1, nv = A.nvel;
     int nn = 1;
     for (int a = 0; a < A.dim; ++a) nn *= np;
     double vol = 1.0;

@@ -22,7 +22,7 @@ struct SetupArgs {
 };
 
 struct PointArgs {
-    int dim, degree, m, system;
+    int dim, degree, m, system, nvel;
     long long nodes;
     double lambda, gamma;
     double adv[3];
@@ -42,6 +42,45 @@ struct DefectArgs {
 };
 
 typedef void (*StepKernel)(Inst);
+
+// ---- d + 1 velocity sets (kin_simplex.cu) ----
+constexpr int kSxMaxNN = 27;      // (p+1)^d <= 27 (3D p <= 2, 2D p <= 3)
+constexpr int kSxThreads = 64;
+
+struct SxSetupArgs {
+    int dim, degree;
+    double lambda, dt;
+    double h[3];
+    int stride;          // elements per velocity record
+    double* c64;         // [d+1][stride] FP64 records
+    float* c32;          // FP32 copy (NULL for FP64)
+    double* minv;        // [(d+1)^2] inverse moment matrix
+    double* work;        // [(d+1)][2 kSxMaxNN^2] scratch
+};
+
+struct SxArgs {
+    void* f;
+    const void* coef;             // T records of sx_setup_kernel
+    const void* tr_in[3];         // per axis: [pop][NS_a][glines_a]
+    void* tr_out[3];
+    long long nodes;
+    long long glines[3];
+    long long trace_total;        // entries written by the trace pass
+    int n[3], L[3], NS[3];
+    int vsgn[4][3];               // sign of V_k along each axis (+1, -1, 0)
+    int dim, degree, nn, m, nvel, npop, system;
+    int coef_stride;
+    int final_iter;
+    double omega, gamma;
+    double adv[3];
+    double minv[16];
+};
+
+cudaError_t sx_launch_setup(const SxSetupArgs& a, cudaStream_t st);
+cudaError_t sx_launch_trace0(const SxArgs& a, int prec, cudaStream_t st);
+cudaError_t sx_launch_sweep(const SxArgs& a, int prec, size_t smem, cudaStream_t st);
+cudaError_t sx_launch_relax(const SxArgs& a, int prec, cudaStream_t st);
+cudaError_t sx_launch_init(const SxArgs& a, const double* W, int prec, cudaStream_t st);
 
 cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st);
 cudaError_t launch_init(const PointArgs& a, const double* W, void* f, int prec, cudaStream_t st);

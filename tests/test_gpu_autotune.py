@@ -34,4 +34,5 @@ def test_tuned_schedule_same_result(kin, tmp_path):
             ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
             ctx.step(5)
             outs.append(ctx.get_state())
-    assert np.abs(outs[0] - outs[1]).max() / np.abs(outs[0]).max() < 1e-6
+    # FP32: the look-back folds a schedule-dependent number of block summaries
+    assert np.abs(outs[0] - outs[1]).max() / np.abs(outs[0]).max() < 1e-5

@@ -1,0 +1,70 @@
+"""GPU parity for the paper's d + 1 velocity sets (D2Q3, Sec. 2.4; D3Q4,
+Sec. 6.1.3): diagonal velocities, anti-diagonal wavefront sweeps and
+corner-sharing subdomains, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests.test_gpu_parity import TOL32, TOL64, oracle_run, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kin():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_11010_gb300 import build
+    build.build()
+    import paper_2212_11010_gb300 as kin
+    kin.load_library()
+    return kin
+
+
+CASES = [
+    lambda prec: workloads.with_(workloads.densitywave2d(seed=1, n=16, degree=2, tiles=2, dt_mult=20.0,
+                                                         velset=1, precision=prec), tiles=(2, 2)),
+    lambda prec: workloads.with_(workloads.densitywave2d(seed=2, n=12, degree=1, tiles=1, dt_mult=30.0,
+                                                         velset=1, precision=prec), tiles=(3, 2), iters=2),
+    lambda prec: workloads.with_(workloads.densitywave2d(seed=3, n=8, degree=3, tiles=2, dt_mult=10.0,
+                                                         velset=1, precision=prec), tiles=(2, 1), iters=1),
+    lambda prec: workloads.with_(workloads.densitywave3d(seed=4, n=8, degree=1, tiles=2, dt_mult=20.0,
+                                                         velset=1, precision=prec), tiles=(2, 2, 2)),
+    lambda prec: workloads.with_(workloads.densitywave3d(seed=5, n=4, degree=2, tiles=1, dt_mult=10.0,
+                                                         velset=1, precision=prec), tiles=(1, 2, 1)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_simplex_sets_match_oracle(kin, case, prec):
+    w = CASES[case](prec)
+    steps = 4
+    with kin.Context.from_workload(w) as ctx:
+        assert ctx.info.nvel == w.dim + 1
+        ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+        ctx.step(steps)
+        W = ctx.get_state()
+        mass = ctx.diag()[0]
+    _, Wo = oracle_run(w, steps)
+    l2, linf = rel_errors(w, W, Wo)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert l2 < tol and linf < tol, (l2, linf)
+    P = oracle.Problem(**w.oracle_kwargs())
+    mo = oracle.mass(P, Wo)
+    np.testing.assert_allclose(mass, mo, rtol=tol * 10, atol=tol * 10)
+
+
+def test_simplex_errors(kin):
+    w = workloads.densitywave2d(seed=1, n=256, degree=3, tiles=1, velset=1)
+    with pytest.raises(kin.KinError) as ei:
+        kin.Context.from_workload(w)          # one subdomain of 256^2 cells does not fit
+    assert ei.value.status == kin.KIN_EINVAL
+    w = workloads.with_(workloads.densitywave2d(seed=1, n=16, degree=1, tiles=2, velset=1), tiles=(2, 2))
+    with kin.Context.from_workload(w) as ctx:
+        ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+        with pytest.raises(kin.KinError) as ei:
+            kin.kin_batch_create([ctx.ctx])
+        assert ei.value.status == kin.KIN_EINVAL

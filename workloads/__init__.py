@@ -171,7 +171,7 @@ def _vortex_fields(X, Y, xc, yc, eps, gamma, box, uinf, vinf):
 
 def vortex2d(seed: int = 0, n: int = 256, degree: int = 2, tiles: int = 8, iters: int = 3,
              dt_mult: float = 5.0, omega: float = 2.0, steps: int = 200,
-             precision: str = "f32", box: float = 10.0) -> Workload:
+             precision: str = "f32", box: float = 10.0, velset: int = 0) -> Workload:
     rng = np.random.default_rng(seed)
     xc, yc = rng.uniform(0.0, box, size=2)
     eps = rng.uniform(3.0, 5.0)
@@ -181,7 +181,7 @@ def vortex2d(seed: int = 0, n: int = 256, degree: int = 2, tiles: int = 8, iters
     X, Y = xyz[:, 0], xyz[:, 1]
     rho, vel, pr = _vortex_fields(X, Y, xc, yc, eps, gamma, box, uinf, vinf)
     amax = _max_speed(rho, vel, pr, gamma)
-    lam = 1.1 * 2 * amax
+    lam = (SIMPLEX_LAMBDA[2] if velset == 1 else 1.1 * 2) * amax
     h = box / n
     dt = dt_mult * h / ((2 * degree + 1) * 2 * amax)
 
@@ -191,7 +191,8 @@ def vortex2d(seed: int = 0, n: int = 256, degree: int = 2, tiles: int = 8, iters
 
     W0 = _euler_conserved(rho, vel, pr, gamma)
     return Workload("vortex2d", 2, (n, n), (0.0, 0.0), (box, box), degree, EULER, lam, dt, omega,
-                    gamma, (0.0, 0.0, 0.0), _tiles(tiles, 2), iters, steps, precision, W0, exact)
+                    gamma, (0.0, 0.0, 0.0), _tiles(tiles, 2), iters, steps, precision, W0, exact,
+                    velset)
 
 
 # Kinetic speed factor for the d + 1 velocity sets (lambda = factor * a_max):
