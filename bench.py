@@ -8,8 +8,9 @@ Workload (default): 2D compressible Euler, isentropic vortex on [0,10]^2,
 256 x 256 cells, DG degree 2 (3 x 3 Gauss-Lobatto nodes), D2Q4 (16
 populations per node), dt = 5 x the explicit DG limit, 8 x 8 subdomains,
 FP32 kinetic state: 9,437,184 kinetic DOF (37.7 MB).  The state is smaller
-than L2, so L2 is flushed (a 256 MB write) before every timed step and only
-the step kernel itself is inside the CUDA-event window.
+than L2, so L2 is flushed before every timed step -- a 256 MB write, then a
+256 MB read so that the written lines are back in HBM -- and only the step
+kernel itself is inside the CUDA-event window.
 
 Metric: kinetic-DOF updates per second (one kinetic DOF = one nodal value of
 one population advanced by one full step).
@@ -251,10 +252,16 @@ def run_ours(args):
     esize = 4 if prec == "f32" else 8
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clean = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sink = torch.empty(1, dtype=torch.float32, device="cuda")
 
     def flush_l2():
+        # write a buffer larger than L2, then read another one: the write
+        # evicts the state; the read makes the write's dirty lines go back to
+        # HBM before the timed step, so the step pays only for its own traffic
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
+            torch.sum(clean, dim=0, keepdim=True, out=sink)
 
     # warm-up
     for _ in range(args.warmup):
@@ -322,7 +329,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
             "config": {"workload": desc, "kinetic_dofs": dofs, "state_bytes": fbytes,
-                       "l2": "flushed (256 MB write) before every timed step",
+                       "l2": "flushed before every timed step (256 MB write, then 256 MB read so the "
+                             "written lines are back in HBM before the step; untimed)",
                        "block": list(ctx.info.block), "grid": ctx.info.grid,
                        "smem_bytes": ctx.info.smem_bytes,
                        "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu"},
