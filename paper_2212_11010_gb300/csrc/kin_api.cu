@@ -301,7 +301,9 @@ static cudaError_t configure_launch(kin_ctx* c)
     FixedKernel fk{nullptr, nullptr, 0, 0};
     if (c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B);
     if (c->dim == 3) fk = fixed_kernel_d3(c->degree, c->system, c->precision, c->B);
-    c->fixed = fk.fn && tma && (c->want_threads == 0 || c->want_threads == fk.threads) && c->want_stages != 2;
+    // (the bounded-wait test hook lives in the bulk-copy path of the generic kernel)
+    c->fixed = fk.fn && tma && (c->want_threads == 0 || c->want_threads == fk.threads) && c->want_stages != 2 &&
+               !(c->debug_flags & KIN_DEBUG_STALL_LOAD);
     if (c->fixed) {
         c->kfn = fk.fn;
         c->threads = fk.threads;

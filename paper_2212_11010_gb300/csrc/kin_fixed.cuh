@@ -13,6 +13,8 @@
 //     warp sweeps lines of a single direction with no per-cell selects.
 #pragma once
 
+#include <type_traits>
+
 #include "kin_device.cuh"
 
 namespace kin {
@@ -177,14 +179,52 @@ __device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, in
     constexpr int DIR = 2 * A + SGN;
 
     if (MODE == 0) {
-        // look-back inflows (before the tile's data has arrived)
+        // look-back inflows (before the tile's data has arrived).  The block
+        // index q, subdomain S and the walk over the summary blocks are the
+        // same for every line of this (axis, sign): computed once, then every
+        // step of the walk loads one summary per line of this thread, so the
+        // loads of all its lines are in flight together.
+        const int nbk = I.nblk[A], nbs = I.nb[A], NSa = I.NS[A], K = I.iters;
+        const int q = SGN == 0 ? bidx : nbk - 1 - bidx;
+        const int Sd = q / nbs, r = q - Sd * nbs;
+        int s0 = (Sd - K) % NSa;
+        if (s0 < 0) s0 += NSa;
+        const long long gl = I.ax[A].glines;
+        const int cnt = (K - 1) * nbs + r;
+        int qj = (s0 + 1 == NSa) ? 0 : (s0 + 1) * nbs;
+        const T* __restrict__ sig = static_cast<const T*>(I.sig_in);
+        const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)s0 * gl;
+        const T RB = coef_of(I, DIR, kOffRhoB, T(0));
+        long long off[KPT];
+        constexpr bool RAGGED = ITEMS % HALF != 0;
+        const bool last_ok = !RAGGED || hid + (KPT - 1) * HALF < ITEMS;
 #pragma unroll
         for (int k = 0; k < KPT; ++k) {
             const int it = hid + k * HALF;
-            if (ITEMS % HALF != 0 && it >= ITEMS) break;
             const int v = it / LP, line = it % LP;
-            const int pop = (2 * A + SGN) * M + v;
-            tr[k] = chain_inflow<T>(I, A, SGN, bidx, pop, fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2));
+            const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
+            const int pop = DIR * M + v;
+            off[k] = (long long)pop * I.sig_stride + gline;
+            if (k < KPT - 1 || last_ok) tr[k] = __ldg(raw + (long long)pop * I.raw_stride + gline);
+        }
+        // the walk in chunks of JC blocks: the JC x KPT loads of a chunk are
+        // issued before any of them is folded
+        constexpr int JC = KPT >= 8 ? 1 : 8 / KPT;
+        for (int j0 = 0; j0 < cnt; j0 += JC) {
+            T val[JC][KPT];
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj) {
+                const T* __restrict__ base = sig + (long long)qj * gl;
+#pragma unroll
+                for (int k = 0; k < KPT; ++k)
+                    val[jj][k] = (j0 + jj < cnt && (k < KPT - 1 || last_ok)) ? __ldg(base + off[k]) : T(0);
+                if (++qj == nbk) qj = 0;
+            }
+#pragma unroll
+            for (int jj = 0; jj < JC; ++jj)
+                if (j0 + jj < cnt)
+#pragma unroll
+                    for (int k = 0; k < KPT; ++k) tr[k] = fma(RB, tr[k], val[jj][k]);
         }
     } else if (MODE == 1) {
         T Pm[NP][NP], g[NP];
@@ -225,6 +265,13 @@ __device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, in
 #pragma unroll
         for (int j = 0; j < NP; ++j) prow[j] = coef_of(I, DIR, kOffProw + j, T(0));
         const T rho = coef_of(I, DIR, kOffRho, T(0));
+        const int nbk = I.nblk[A], nbs = I.nb[A];
+        const int q = SGN == 0 ? bidx : nbk - 1 - bidx;
+        const int Sd = q / nbs;
+        const bool writes_raw = q - Sd * nbs == nbs - 1;    // downwind-most block of its subdomain
+        const long long gl = I.ax[A].glines;
+        T* __restrict__ sig = static_cast<T*>(I.sig_out) + (long long)q * gl;
+        T* __restrict__ raw = static_cast<T*>(I.raw_out) + (long long)Sd * gl;
 #pragma unroll
         for (int k = 0; k < KPT; ++k) {
             const int it = hid + k * HALF;
@@ -245,8 +292,9 @@ __device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, in
                 t = fma(rho, t, acc);
                 last = SGN == 0 ? u[NP - 1] : u[0];
             }
-            write_summary<T>(I, A, SGN, bidx, pop, fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2), t,
-                             last);
+            const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
+            sig[(long long)pop * I.sig_stride + gline] = t;
+            if (writes_raw) raw[(long long)pop * I.raw_stride + gline] = last;
         }
     }
 }
@@ -336,76 +384,189 @@ __device__ __forceinline__ void fixed_relax(const Inst& I, T* s)
     }
 }
 
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, bool STORE>
-__device__ __forceinline__ void fixed_issue_copies(const Inst& I, int org0, int org1, int org2, T* s, uint64_t* bar)
+// Packed FP32 pairs (two lanes per instruction; each lane is the scalar IEEE
+// operation of the same name).
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// The relaxation of fixed_relax on two neighbouring nodes at a time (FP32,
+// rows of even length): the populations of a node pair are one 8-byte
+// shared-memory word each, and every step is a packed pair operation.
+template <int D, int P, int SYS, int B0, int B1, int B2, int NTH>
+__device__ __forceinline__ void fixed_relax_pairs(const Inst& I, float* s)
 {
-    using S = Shape<D, P, SYS, T, B0, B1, B2>;
-    constexpr int NCH = S::NPOP * S::NROWS;
-    constexpr unsigned BYTES = (unsigned)(S::ROWLEN * sizeof(T));
-    T* f = static_cast<T*>(I.f);
-    const int lane = threadIdx.x;
-    if (!STORE) {
-        if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)NCH * BYTES + (I.debug_stall ? 16u : 0u));
-        __syncwarp();
-    }
+    using S = Shape<D, P, SYS, float, B0, B1, B2>;
+    constexpr int M = S::M, NV = 2 * D, NPOP = S::NPOP;
+    constexpr int NPAIR = S::NODES / 2;
+    static_assert(S::ROWLEN % 2 == 0 && S::RSTR % 2 == 0 && S::PSTR % 2 == 0, "node pairs must be 8-byte words");
+    const bool two = I.omega == 2.0;
+    const float2 om = f2((float)I.omega), omc = f2(1.0f - (float)I.omega);
+    const float2 inv2d = f2((float)(1.0 / (2.0 * D)));
+    const float2 inv2l = f2((float)(1.0 / (2.0 * I.lambda)));
+    const float2 gm1 = f2((float)(I.gamma - 1.0));
+    const float2 twof = f2(2.0f);
 #pragma unroll
-    for (int k = 0; k < (NCH + 31) / 32; ++k) {
-        const int ch = lane + 32 * k;
-        if (NCH % 32 != 0 && ch >= NCH) break;
-        const int pop = ch / S::NROWS, row = ch % S::NROWS;
-        const int ly = row % B1, lz = row / B1;
-        const long long g = (long long)pop * I.nodes
-            + (((long long)(org2 + lz) * (D > 1 ? I.n[1] : 1) + (org1 + ly)) * I.n[0] + org0) * S::NN;
-        T* sp = s + pop * S::PSTR + row * S::RSTR;
-        if (STORE) bulk_s2g(f + g, sp, BYTES);
-        else bulk_g2s(sp, f + g, BYTES, bar);
+    for (int k = 0; k < (NPAIR + NTH - 1) / NTH; ++k) {
+        const int pr = threadIdx.x + k * NTH;
+        if (NPAIR % NTH != 0 && pr >= NPAIR) break;
+        const int nd = 2 * pr;
+        const int o = (nd / S::ROWLEN) * S::RSTR + nd % S::ROWLEN;
+        // W = sum_k f_k, compensated (the first term starts the sum exactly);
+        // with many populations the pairs are read again for the update
+        // instead of being held in registers
+        constexpr bool HOLD = NPOP < 16;
+        float2 fk[HOLD ? NPOP : 1];
+        const unsigned sbase = (unsigned)__cvta_generic_to_shared(s + o);
+        auto ld = [&](int pp) {
+            if constexpr (HOLD) {
+                return *reinterpret_cast<const float2*>(s + pp * S::PSTR + o);
+            } else {
+                // a fresh read each time (kept out of registers between the passes)
+                float2 v;
+                asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                             : "=f"(v.x), "=f"(v.y)
+                             : "r"(sbase + (unsigned)(pp * S::PSTR * 4))
+                             : "memory");
+                return v;
+            }
+        };
+        if constexpr (HOLD) {
+#pragma unroll
+            for (int pp = 0; pp < NPOP; ++pp) fk[pp] = ld(pp);
+        }
+        auto get = [&](int pp) { if constexpr (HOLD) return fk[pp]; else return ld(pp); };
+        float2 W[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            float2 sum = get(v), c = f2(0.0f);
+#pragma unroll
+            for (int kk = 1; kk < NV; ++kk) {
+                const float2 y = kk == 1 ? get(kk * M + v) : sub2(get(kk * M + v), c);
+                const float2 t = add2(sum, y);
+                c = sub2(sub2(t, sum), y);
+                sum = t;
+            }
+            W[v] = sum;
+        }
+        float2 inv = f2(0.0f), pres = f2(0.0f);
+        if (SYS == kEuler) {
+            inv = make_float2(__frcp_rn(W[0].x), __frcp_rn(W[0].y));
+            float2 ke = mul2(W[1], W[1]);
+#pragma unroll
+            for (int b = 1; b < D; ++b) ke = fma2(W[1 + b], W[1 + b], ke);
+            pres = mul2(gm1, sub2(W[1 + D], mul2(mul2(f2(0.5f), ke), inv)));
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            float2 Q[M];
+            if (SYS == kAdvection) {
+                Q[0] = mul2(f2((float)I.adv[a]), W[0]);
+            } else {
+                const float2 ua = mul2(W[1 + a], inv);
+                Q[0] = W[1 + a];
+#pragma unroll
+                for (int b = 0; b < D; ++b) Q[1 + b] = b == a ? fma2(W[1 + b], ua, pres) : mul2(W[1 + b], ua);
+                Q[1 + D] = mul2(add2(W[1 + D], pres), ua);
+            }
+#pragma unroll
+            for (int v = 0; v < M; ++v) {
+                const float2 base = mul2(W[v], inv2d);
+                const float2 hq = mul2(Q[v], inv2l);
+                const int ip = (2 * a) * M + v, im = (2 * a + 1) * M + v;
+                const float2 fp = get(ip), fm = get(im);
+                float2 np_, nm_;
+                if (two) {
+                    np_ = fma2(twof, add2(base, hq), make_float2(-fp.x, -fp.y));
+                    nm_ = fma2(twof, sub2(base, hq), make_float2(-fm.x, -fm.y));
+                } else {
+                    np_ = fma2(om, add2(base, hq), mul2(omc, fp));
+                    nm_ = fma2(om, sub2(base, hq), mul2(omc, fm));
+                }
+                *reinterpret_cast<float2*>(s + ip * S::PSTR + o) = np_;
+                *reinterpret_cast<float2*>(s + im * S::PSTR + o) = nm_;
+            }
+        }
     }
-    if (STORE) bulk_commit();
 }
 
-// One tile of the fixed-shape step: issue the bulk loads, fold the look-back
-// inflows while they fly, wait (bounded), sweep, relax, write the summaries
-// and issue the bulk stores.  'i' counts the tiles this thread block has
-// processed (mbarrier phase).  Returns false if the bounded wait gave up.
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
-__device__ __forceinline__ bool fixed_tile(const Inst& I, int t, int i, T* s, uint64_t* bar, int* flag,
-                                           T (&tr)[3][KM])
+// Tile rows move as 16-byte chunks through the load/store units, spread over
+// all threads: cp.async (global -> shared) for the loads, shared -> register
+// -> global for the stores.  (Bulk copies of whole rows go through the
+// per-SM copy engine one short row at a time, which caps loads plus stores
+// of rows this short well below the HBM rate.)  Chunks are grouped by G
+// populations per pass so that each thread's (row, chunk) decode is done once.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, bool STORE>
+__device__ __forceinline__ void fixed_copy(const Inst& I, int org0, int org1, int org2, T* s)
 {
-    const int tid = threadIdx.x;
-    const bool warp0 = tid < 32;
+    using S = Shape<D, P, SYS, T, B0, B1, B2>;
+    static_assert(S::ROWLEN % S::VEC == 0 && S::RSTR % S::VEC == 0 && S::PSTR % S::VEC == 0,
+                  "rows must be whole 16-byte chunks");
+    constexpr int CPR = S::ROWLEN / S::VEC;                 // chunks per row
+    constexpr int PER_POP = S::NROWS * CPR;
+    constexpr int G = NTH / PER_POP >= 1 ? NTH / PER_POP : 1;
+    constexpr int GC = G * PER_POP;                          // chunks of one population group
+    constexpr int KR = (GC + NTH - 1) / NTH;
+    constexpr int NG = (S::NPOP + G - 1) / G;
+    const long long rowy = (long long)I.n[0] * S::NN;       // elements from row y to y + 1
+    const long long rowz = (long long)(D > 1 ? I.n[1] : 1) * rowy;
+    T* fb = static_cast<T*>(I.f) + (((long long)org2 * (D > 1 ? I.n[1] : 1) + org1) * I.n[0] + org0) * S::NN;
+    int soff[KR], pg[KR];
+    long long goff[KR];
+    bool ok[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+        const int c = threadIdx.x + k * NTH;
+        ok[k] = GC % NTH == 0 || c < GC;
+        const int cc = ok[k] ? c : 0;
+        pg[k] = cc / PER_POP;
+        const int rem = cc - pg[k] * PER_POP;
+        const int row = rem / CPR, cq = rem - (rem / CPR) * CPR;
+        const int ly = row % B1, lz = row / B1;
+        soff[k] = pg[k] * S::PSTR + row * S::RSTR + cq * S::VEC;
+        goff[k] = (long long)pg[k] * I.nodes + lz * rowz + ly * rowy + cq * S::VEC;
+    }
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            if (!ok[k] || (S::NPOP % G != 0 && g * G + pg[k] >= S::NPOP)) continue;
+            T* sp = s + g * G * S::PSTR + soff[k];
+            T* gp = fb + (long long)(g * G) * I.nodes + goff[k];
+            if (STORE) *reinterpret_cast<uint4*>(gp) = *reinterpret_cast<const uint4*>(sp);
+            else cp16_g2s(sp, gp);
+        }
+    }
+    if (!STORE) cp_commit();
+}
+
+// One tile of the fixed-shape step: start the loads, fold the look-back
+// inflows while they fly, wait for this thread's copies and meet at a
+// barrier, sweep, relax, store, write the summaries, and meet again before
+// the buffer is reused.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
+__device__ __forceinline__ void fixed_tile(const Inst& I, int t, T* s, T (&tr)[3][KM])
+{
     const TileXYZ c = tile_xyz(I, t);
     const int org0 = c.bx * B0, org1 = c.by * B1, org2 = c.bz * B2;
-    if (warp0) {
-        if (i > 0) {
-            bulk_wait_read();   // previous tile's stores have read the buffer
-            __syncwarp();
-        }
-        fixed_issue_copies<D, P, SYS, T, B0, B1, B2, false>(I, org0, org1, org2, s, bar);
-    }
+    fixed_copy<D, P, SYS, T, B0, B1, B2, NTH, false>(I, org0, org1, org2, s);
     if (I.mode == 0) fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 0, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
-    if (tid == 0) *flag = mbar_wait_bounded(bar, i & 1, I.wait_cycles) ? 1 : 0;
+    cp_wait_all();
     __syncthreads();
-    if (*flag == 0) {
-        // give up: report, wait (bounded) for the copies still in flight
-        if (tid == 0) {
-            if (I.err) atomicOr(I.err, kErrLoadTimeout);
-            mbar_wait_bounded(bar, i & 1, I.wait_cycles);
-        }
-        if (warp0) bulk_wait_all();
-        return false;
-    }
-    (void)mbar_try_wait(bar, i & 1);
     if (I.mode == 0) {
         fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 1, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
         __syncthreads();
-        fixed_relax<D, P, SYS, T, B0, B1, B2, NTH>(I, s);
+        if constexpr (std::is_same<T, float>::value && Shape<D, P, SYS, T, B0, B1, B2>::ROWLEN % 2 == 0)
+            fixed_relax_pairs<D, P, SYS, B0, B1, B2, NTH>(I, s);
+        else
+            fixed_relax<D, P, SYS, T, B0, B1, B2, NTH>(I, s);
         __syncthreads();
+        fixed_copy<D, P, SYS, T, B0, B1, B2, NTH, true>(I, org0, org1, org2, s);
     }
     fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 2, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
-    if (I.mode == 0) fence_proxy_async_smem();
     __syncthreads();
-    if (I.mode == 0 && warp0) fixed_issue_copies<D, P, SYS, T, B0, B1, B2, true>(I, org0, org1, org2, s, bar);
-    return true;
 }
 
 // Fixed-shape step kernel: one tile per loop iteration, one shared-memory
@@ -415,22 +576,11 @@ __global__ void __launch_bounds__(NTH, MINB) step_kernel_fixed(const __grid_cons
 {
     using S = Shape<D, P, SYS, T, B0, B1, B2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int flag;
     T* s = reinterpret_cast<T*>(smem_raw);
     constexpr int KM = S::kpt_max(NTH / 2);
     T tr[3][KM];      // look-back inflows of this thread's lines
     const int ntiles = I.nblk[0] * I.nblk[1] * I.nblk[2];
-    int t = blockIdx.x;
-    if (t >= ntiles) return;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    for (int i = 0; t < ntiles; ++i, t += gridDim.x)
-        if (!fixed_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, t, i, s, &bar, &flag, tr)) return;
-    if (threadIdx.x < 32) bulk_wait_all();
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) fixed_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, t, s, tr);
 }
 
 // Batched fixed-shape step kernel: the thread blocks walk a work list of
@@ -443,33 +593,23 @@ __global__ void __launch_bounds__(NTH, MINB)
 {
     using S = Shape<D, P, SYS, T, B0, B1, B2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int flag;
     __shared__ __align__(16) Inst Ish;
     T* s = reinterpret_cast<T*>(smem_raw);
     constexpr int KM = S::kpt_max(NTH / 2);
     T tr[3][KM];
-    int w = blockIdx.x;
-    if (w >= nwork) return;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
     int have = -1;
-    for (int i = 0; w < nwork; ++i, w += gridDim.x) {
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
         const int2 wk = work[w];
         if (wk.x != have) {
-            // warp 0 may still read the record while issuing the previous tile's stores
-            __syncthreads();
+            // every thread has finished the previous tile (barrier at its end)
             const int4* src = reinterpret_cast<const int4*>(insts + wk.x);
             int4* dst = reinterpret_cast<int4*>(&Ish);
             for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 16); k += NTH) dst[k] = src[k];
             have = wk.x;
+            __syncthreads();
         }
-        __syncthreads();
-        if (!fixed_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(Ish, wk.y, i, s, &bar, &flag, tr)) return;
+        fixed_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(Ish, wk.y, s, tr);
     }
-    if (threadIdx.x < 32) bulk_wait_all();
 }
 
 }  // namespace kin

@@ -128,4 +128,17 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+
+// ---- 16-byte asynchronous copies through the load/store units ----
+// global -> shared without register staging (cp.async, L2 only); completion
+// is per thread (cp_wait_all), visibility to the block needs a barrier.
+__device__ __forceinline__ void cp16_g2s(void* sdst, const void* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 }  // namespace kin

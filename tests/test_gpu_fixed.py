@@ -55,10 +55,13 @@ def test_fixed_shape_matches_oracle_and_generic(kin, shape):
     l2, linf = rel_errors(w, W, Wo)
     tol = TOL32 if prec == "f32" else TOL64
     assert l2 < tol and linf < tol, (l2, linf)
-    # the generic kernel on the same block (a different thread count forces it)
+    # the generic kernel on the same block (a different thread count forces it).
+    # The two evaluate the same formulas with different FMA contractions and
+    # (in FP32) packed pair arithmetic, so they agree to a few dozen ulp after
+    # four steps, not bit for bit.
     Wg, fg, infog = _run(kin, w, block, steps, threads=256 if info.threads != 256 else 128)
     assert infog.specialised == 0
-    assert np.abs(f - fg).max() / np.abs(fg).max() < (1e-6 if prec == "f32" else 1e-14)
+    assert np.abs(f - fg).max() / np.abs(fg).max() < (5e-6 if prec == "f32" else 1e-14)
 
 
 def test_default_block_uses_fixed_kernel_for_benchmarked_workload(kin):
