@@ -231,6 +231,9 @@ static Inst make_inst(const kin_ctx* c, int mode)
         I.ax[a].e1 = make_fastdiv((unsigned)(a == 0 ? c->B[1] : c->B[0]));
         I.ax[a].glines = (long long)(c->cells / c->n[a]) * tn;
     }
+    I.fd_nblk0 = make_fastdiv((unsigned)c->nblk[0]);
+    I.fd_nblk01 = make_fastdiv((unsigned)(c->nblk[0] * c->nblk[1]));
+    for (int a = 0; a < 3; ++a) I.fd_nb[a] = make_fastdiv((unsigned)c->nb[a]);
     I.fd_nrows = make_fastdiv((unsigned)(c->B[1] * c->B[2]));
     I.fd_B1 = make_fastdiv((unsigned)c->B[1]);
     I.fd_rowlen = make_fastdiv((unsigned)(c->B[0] * c->NN));
@@ -299,15 +302,22 @@ static cudaError_t configure_launch(kin_ctx* c)
     const bool tma = rows_are_16b_aligned(c);
     // fixed-shape kernel: same result, compile-time shape (bulk copies, one stage)
     FixedKernel fk{nullptr, nullptr, 0, 0};
-    if (c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B);
-    if (c->dim == 3) fk = fixed_kernel_d3(c->degree, c->system, c->precision, c->B);
+    int fstages = 1;
+    if (c->dim >= 2)
+        fstages = c->want_stages ? c->want_stages
+                                 : fixed_default_stages(c->dim, c->degree, c->system, c->precision, c->B);
+    if (c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B, fstages);
+    if (c->dim == 3) fk = fixed_kernel_d3(c->degree, c->system, c->precision, c->B, fstages);
     // (the bounded-wait test hook lives in the bulk-copy path of the generic kernel)
-    c->fixed = fk.fn && tma && (c->want_threads == 0 || c->want_threads == fk.threads) && c->want_stages != 2 &&
+    // (the fixed kernels index the block summaries with 32-bit offsets)
+    const bool small_summaries = (double)c->sig_stride * c->npop < 2147483647.0;
+    c->fixed = fk.fn && fk.smem <= 227 * 1024 && tma && small_summaries &&
+               (c->want_threads == 0 || c->want_threads == fk.threads) &&
                !(c->debug_flags & KIN_DEBUG_STALL_LOAD);
     if (c->fixed) {
         c->kfn = fk.fn;
         c->threads = fk.threads;
-        c->stages = 1;
+        c->stages = fstages;
         c->smem = (int)fk.smem;
     } else {
         c->kfn = pick_kernel(c->dim, c->degree, c->system, c->precision);
@@ -1066,8 +1076,8 @@ extern "C" kin_status kin_batch_create(kin_ctx* const* members, int count, void*
     for (int i = 0; i < count; ++i) {
         kin_ctx* c = b->members[i];
         FixedKernel fk{nullptr, nullptr, 0, 0};
-        if (c->fixed && c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B);
-        if (c->fixed && c->dim == 3) fk = fixed_kernel_d3(c->degree, c->system, c->precision, c->B);
+        if (c->fixed && c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B, c->stages);
+        if (c->fixed && c->dim == 3) fk = fixed_kernel_d3(c->degree, c->system, c->precision, c->B, c->stages);
         if (!fk.batch_fn) {
             b->solo.push_back(i);
             continue;

@@ -99,9 +99,12 @@ struct FixedKernel {
     size_t smem;
 };
 
-// Fixed-shape kernel for (degree, system, precision, block) or fn == nullptr.
-FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3]);
-FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3]);
+// Fixed-shape kernel for (degree, system, precision, block) with one or two
+// shared-memory tile buffers, or fn == nullptr.
+FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3], int stages);
+FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3], int stages);
+// Tile buffers the fixed-shape kernel of a shape uses unless asked otherwise.
+int fixed_default_stages(int dim, int degree, int system, int prec, const int B[3]);
 // Preferred fixed block shapes for a (dim, degree, system, precision), best first;
 // returns the count written (at most 4).
 int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3]);

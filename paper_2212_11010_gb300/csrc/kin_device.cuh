@@ -85,6 +85,9 @@ struct __align__(16) Inst {
     int nb[3];               // blocks per subdomain along each axis
     int NS[3];               // subdomains along each axis
     AxisInfo ax[3];
+    FastDiv fd_nblk0;        // nblk[0]
+    FastDiv fd_nblk01;       // nblk[0] * nblk[1]
+    FastDiv fd_nb[3];        // nb[a]
     FastDiv fd_nrows;        // B[1] * B[2]
     FastDiv fd_B1;           // B[1]
     FastDiv fd_rowlen;       // B[0] * nodes per cell
@@ -357,6 +360,20 @@ __device__ __forceinline__ void lines_all(const Inst& I, int bx, int by, int bz,
                                               tin + items_of_axis<D, P, SYS, 0>(I) + items_of_axis<D, P, SYS, 1>(I));
 }
 
+struct TileXYZ {
+    int bx, by, bz;
+};
+
+__device__ __forceinline__ TileXYZ tile_xyz(const Inst& I, int t)
+{
+    TileXYZ c;
+    c.bz = (int)fdiv((unsigned)t, I.fd_nblk01);
+    const int rem = t - c.bz * (int)I.fd_nblk01.d;
+    c.by = (int)fdiv((unsigned)rem, I.fd_nblk0);
+    c.bx = rem - c.by * (int)I.fd_nblk0.d;
+    return c;
+}
+
 // Relaxation at every node of the block (eq. over_relaxation) with the 2d
 // velocity equilibria M_{a,+-} = W/(2d) +- Q^a(W)/(2 lambda).
 template <int D, int P, int SYS, typename T>
@@ -438,19 +455,6 @@ __device__ __forceinline__ long long row_offset(const Inst& I, int pop, int row,
     }
     const long long cellrow = ((long long)(z0 + lz) * (D > 1 ? I.n[1] : 1) + (y0 + ly)) * I.n[0] + x0;
     return (long long)pop * I.nodes + cellrow * NN;
-}
-
-struct TileXYZ {
-    int bx, by, bz;
-};
-
-__device__ __forceinline__ TileXYZ tile_xyz(const Inst& I, int t)
-{
-    TileXYZ c;
-    c.bx = t % I.nblk[0];
-    c.by = (t / I.nblk[0]) % I.nblk[1];
-    c.bz = t / (I.nblk[0] * I.nblk[1]);
-    return c;
 }
 
 // Bulk loads of every row of tile t into s, completing on bar (warp 0 only).

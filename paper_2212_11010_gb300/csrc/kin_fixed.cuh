@@ -178,55 +178,7 @@ __device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, in
     constexpr int NS = S::nstep(A);
     constexpr int DIR = 2 * A + SGN;
 
-    if (MODE == 0) {
-        // look-back inflows (before the tile's data has arrived).  The block
-        // index q, subdomain S and the walk over the summary blocks are the
-        // same for every line of this (axis, sign): computed once, then every
-        // step of the walk loads one summary per line of this thread, so the
-        // loads of all its lines are in flight together.
-        const int nbk = I.nblk[A], nbs = I.nb[A], NSa = I.NS[A], K = I.iters;
-        const int q = SGN == 0 ? bidx : nbk - 1 - bidx;
-        const int Sd = q / nbs, r = q - Sd * nbs;
-        int s0 = (Sd - K) % NSa;
-        if (s0 < 0) s0 += NSa;
-        const long long gl = I.ax[A].glines;
-        const int cnt = (K - 1) * nbs + r;
-        int qj = (s0 + 1 == NSa) ? 0 : (s0 + 1) * nbs;
-        const T* __restrict__ sig = static_cast<const T*>(I.sig_in);
-        const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)s0 * gl;
-        const T RB = coef_of(I, DIR, kOffRhoB, T(0));
-        long long off[KPT];
-        constexpr bool RAGGED = ITEMS % HALF != 0;
-        const bool last_ok = !RAGGED || hid + (KPT - 1) * HALF < ITEMS;
-#pragma unroll
-        for (int k = 0; k < KPT; ++k) {
-            const int it = hid + k * HALF;
-            const int v = it / LP, line = it % LP;
-            const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
-            const int pop = DIR * M + v;
-            off[k] = (long long)pop * I.sig_stride + gline;
-            if (k < KPT - 1 || last_ok) tr[k] = __ldg(raw + (long long)pop * I.raw_stride + gline);
-        }
-        // the walk in chunks of JC blocks: the JC x KPT loads of a chunk are
-        // issued before any of them is folded
-        constexpr int JC = KPT >= 8 ? 1 : 8 / KPT;
-        for (int j0 = 0; j0 < cnt; j0 += JC) {
-            T val[JC][KPT];
-#pragma unroll
-            for (int jj = 0; jj < JC; ++jj) {
-                const T* __restrict__ base = sig + (long long)qj * gl;
-#pragma unroll
-                for (int k = 0; k < KPT; ++k)
-                    val[jj][k] = (j0 + jj < cnt && (k < KPT - 1 || last_ok)) ? __ldg(base + off[k]) : T(0);
-                if (++qj == nbk) qj = 0;
-            }
-#pragma unroll
-            for (int jj = 0; jj < JC; ++jj)
-                if (j0 + jj < cnt)
-#pragma unroll
-                    for (int k = 0; k < KPT; ++k) tr[k] = fma(RB, tr[k], val[jj][k]);
-        }
-    } else if (MODE == 1) {
+    if (MODE == 1) {
         T Pm[NP][NP], g[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
@@ -299,8 +251,108 @@ __device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, in
     }
 }
 
-// MODE 0: look-back inflows, 1: transport sweeps, 2: block summaries.  Each
-// sign half runs its own warps (HALF is a multiple of 32).
+// Look-back plan of one axis for this thread's sign: the block index q,
+// subdomain S and the start of the walk over the summary blocks are the same
+// for every line of the (axis, sign); the raw value of subdomain S-K starts
+// every line's fold (see chain_inflow for the meaning).  off[k] receives the
+// 32-bit element offset of line k's summaries (block 0).
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int A, int KM>
+__device__ __forceinline__ void chain_setup(const Inst& I, int hid, int sgn, int org0, int org1, int org2,
+                                            int bidx, T (&tr)[KM], int (&off)[KM], int& qj, int& cnt, T& RB)
+{
+    using S = Shape<D, P, SYS, T, B0, B1, B2>;
+    constexpr int NP = S::NP, M = S::M, HALF = NTH / 2;
+    constexpr int LP = S::lines(A);
+    constexpr int ITEMS = M * LP;
+    constexpr int KPT = S::kpt(A, HALF);
+    const int nbk = I.nblk[A], nbs = I.nb[A], NSa = I.NS[A], K = I.iters;
+    const int q = sgn == 0 ? bidx : nbk - 1 - bidx;
+    const int Sd = (int)fdiv((unsigned)q, I.fd_nb[A]);
+    const int r = q - Sd * nbs;
+    int s0 = Sd - K;
+    while (s0 < 0) s0 += NSa;
+    const long long gl = I.ax[A].glines;
+    cnt = (K - 1) * nbs + r;
+    qj = (s0 + 1 == NSa) ? 0 : (s0 + 1) * nbs;
+    RB = coef_of(I, 2 * A + sgn, kOffRhoB, T(0));
+    const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)s0 * gl;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        const int it = hid + k * HALF;
+        if (k >= KPT || (ITEMS % HALF != 0 && it >= ITEMS)) {
+            off[k] = 0;       // a valid address; the item's result is never used
+            tr[k] = T(0);
+            continue;
+        }
+        const int v = it / LP, line = it % LP;
+        const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
+        const int pop = (2 * A + sgn) * M + v;
+        off[k] = (int)((long long)pop * I.sig_stride + gline);   // fits: checked on the host
+        tr[k] = __ldg(raw + (long long)pop * I.raw_stride + gline);
+    }
+}
+
+// Look-back inflows of all lines of this thread (every axis of its sign),
+// folded while the tile's copies fly.  The walks of all axes advance
+// together one summary block per step: every line keeps the 32-bit element
+// index of its next summary, which moves by the line count of its axis and
+// wraps (periodically) after the last block; the unrolled steps let the
+// loads of several steps be in flight at once.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
+__device__ __forceinline__ void fixed_chain(const Inst& I, int org0, int org1, int org2, int bx, int by, int bz,
+                                            T (&tr)[3][KM])
+{
+    using S = Shape<D, P, SYS, T, B0, B1, B2>;
+    constexpr int HALF = NTH / 2;
+    constexpr int KP[3] = {S::kpt(0, HALF), D > 1 ? S::kpt(1, HALF) : 0, D > 2 ? S::kpt(2, HALF) : 0};
+    const int tid = threadIdx.x;
+    const int sgn = tid < HALF ? 0 : 1;
+    const int hid = tid - sgn * HALF;
+    int idx[3][KM];
+    int qj[3] = {0, 0, 0}, cnt[3] = {0, 0, 0};
+    T RB[3] = {T(0), T(0), T(0)};
+    chain_setup<D, P, SYS, T, B0, B1, B2, NTH, 0, KM>(I, hid, sgn, org0, org1, org2, bx, tr[0], idx[0], qj[0],
+                                                      cnt[0], RB[0]);
+    if constexpr (D > 1)
+        chain_setup<D, P, SYS, T, B0, B1, B2, NTH, 1, KM>(I, hid, sgn, org0, org1, org2, by, tr[1], idx[1],
+                                                          qj[1], cnt[1], RB[1]);
+    if constexpr (D > 2)
+        chain_setup<D, P, SYS, T, B0, B1, B2, NTH, 2, KM>(I, hid, sgn, org0, org1, org2, bz, tr[2], idx[2],
+                                                          qj[2], cnt[2], RB[2]);
+    const T* __restrict__ sig = static_cast<const T*>(I.sig_in);
+    int gl[3], left[3], wrap[3];
+    int maxcnt = 0;
+#pragma unroll
+    for (int A = 0; A < D; ++A) {
+        gl[A] = (int)I.ax[A].glines;
+        left[A] = I.nblk[A] - qj[A];            // steps before the walk wraps to block 0
+        wrap[A] = I.nblk[A] * gl[A];
+#pragma unroll
+        for (int k = 0; k < KM; ++k)
+            if (k < KP[A]) idx[A][k] += qj[A] * gl[A];
+        maxcnt = cnt[A] > maxcnt ? cnt[A] : maxcnt;
+    }
+#pragma unroll 4
+    for (int j = 0; j < maxcnt; ++j) {
+#pragma unroll
+        for (int A = 0; A < D; ++A) {
+            if (j < cnt[A]) {
+                const bool w = --left[A] == 0;
+                const int step = w ? gl[A] - wrap[A] : gl[A];
+                left[A] = w ? I.nblk[A] : left[A];
+#pragma unroll
+                for (int k = 0; k < KM; ++k)
+                    if (k < KP[A]) {
+                        tr[A][k] = fma(RB[A], tr[A][k], __ldg(sig + idx[A][k]));
+                        idx[A][k] += step;
+                    }
+            }
+        }
+    }
+}
+
+// MODE 1: transport sweeps, 2: block summaries.  Each sign half runs its
+// own warps (HALF is a multiple of 32).
 template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MODE, int KM>
 __device__ __forceinline__ void fixed_lines_all(const Inst& I, int org0, int org1, int org2, int bx, int by,
                                                 int bz, T* s, T (&tr)[3][KM])
@@ -542,19 +594,14 @@ __device__ __forceinline__ void fixed_copy(const Inst& I, int org0, int org1, in
     if (!STORE) cp_commit();
 }
 
-// One tile of the fixed-shape step: start the loads, fold the look-back
-// inflows while they fly, wait for this thread's copies and meet at a
-// barrier, sweep, relax, store, write the summaries, and meet again before
-// the buffer is reused.
+// The work of one tile once its data is in shared memory: sweep, relax,
+// store, write the summaries, and meet at a barrier before the buffer is
+// reused.
 template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
-__device__ __forceinline__ void fixed_tile(const Inst& I, int t, T* s, T (&tr)[3][KM])
+__device__ __forceinline__ void fixed_compute(const Inst& I, int t, T* s, T (&tr)[3][KM])
 {
     const TileXYZ c = tile_xyz(I, t);
     const int org0 = c.bx * B0, org1 = c.by * B1, org2 = c.bz * B2;
-    fixed_copy<D, P, SYS, T, B0, B1, B2, NTH, false>(I, org0, org1, org2, s);
-    if (I.mode == 0) fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 0, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
-    cp_wait_all();
-    __syncthreads();
     if (I.mode == 0) {
         fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 1, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
         __syncthreads();
@@ -569,46 +616,90 @@ __device__ __forceinline__ void fixed_tile(const Inst& I, int t, T* s, T (&tr)[3
     __syncthreads();
 }
 
-// Fixed-shape step kernel: one tile per loop iteration, one shared-memory
-// stage; the grid is persistent (blocks walk tiles blockIdx.x + k gridDim.x).
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MINB>
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH>
+__device__ __forceinline__ void fixed_load(const Inst& I, int t, T* s)
+{
+    const TileXYZ c = tile_xyz(I, t);
+    fixed_copy<D, P, SYS, T, B0, B1, B2, NTH, false>(I, c.bx * B0, c.by * B1, c.bz * B2, s);
+}
+
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
+__device__ __forceinline__ void fixed_chain_tile(const Inst& I, int t, T (&tr)[3][KM])
+{
+    const TileXYZ c = tile_xyz(I, t);
+    fixed_chain<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, c.bx * B0, c.by * B1, c.bz * B2, c.bx, c.by, c.bz, tr);
+}
+
+// Fixed-shape step kernel on a persistent grid (blocks walk tiles
+// blockIdx.x + k gridDim.x).  With STG = 1 a tile is loaded, its look-back
+// inflows folded while the copies fly, then computed.  With STG = 2 the
+// block owns two tile buffers: the next tile's copies are issued before the
+// current tile is computed, so loads of one tile overlap the work on the
+// previous one.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MINB, int STG>
 __global__ void __launch_bounds__(NTH, MINB) step_kernel_fixed(const __grid_constant__ Inst I)
 {
     using S = Shape<D, P, SYS, T, B0, B1, B2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* s = reinterpret_cast<T*>(smem_raw);
+    T* const s0 = reinterpret_cast<T*>(smem_raw);
+    T* const s1 = s0 + (STG == 2 ? S::TILE : 0);
     constexpr int KM = S::kpt_max(NTH / 2);
     T tr[3][KM];      // look-back inflows of this thread's lines
     const int ntiles = I.nblk[0] * I.nblk[1] * I.nblk[2];
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) fixed_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, t, s, tr);
+    int t = blockIdx.x;
+    if (t >= ntiles) return;
+    if (STG == 2) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, t, s0);
+    for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
+        T* const cur = (i & 1) ? s1 : s0;
+        if (STG == 1) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, t, cur);
+        if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, t, tr);
+        const int tn = t + gridDim.x;
+        if (STG == 2 && tn < ntiles) {
+            fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, tn, (i & 1) ? s0 : s1);
+            cp_wait_prior();
+        } else {
+            cp_wait_all();
+        }
+        __syncthreads();
+        fixed_compute<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, t, cur, tr);
+    }
 }
 
 // Batched fixed-shape step kernel: the thread blocks walk a work list of
 // (instance, tile) pairs over several independent problems of the same
-// kernel type; each instance's launch record is copied into shared memory
-// when a block moves to a tile of another instance.
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MINB>
+// kernel type, reading each instance's launch record from global memory
+// (read-only for the launch), with the same one- or two-buffer schedule.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MINB, int STG>
 __global__ void __launch_bounds__(NTH, MINB)
     step_kernel_fixed_batch(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork)
 {
     using S = Shape<D, P, SYS, T, B0, B1, B2>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(16) Inst Ish;
-    T* s = reinterpret_cast<T*>(smem_raw);
+    T* const s0 = reinterpret_cast<T*>(smem_raw);
+    T* const s1 = s0 + (STG == 2 ? S::TILE : 0);
     constexpr int KM = S::kpt_max(NTH / 2);
     T tr[3][KM];
-    int have = -1;
-    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
-        const int2 wk = work[w];
-        if (wk.x != have) {
-            // every thread has finished the previous tile (barrier at its end)
-            const int4* src = reinterpret_cast<const int4*>(insts + wk.x);
-            int4* dst = reinterpret_cast<int4*>(&Ish);
-            for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 16); k += NTH) dst[k] = src[k];
-            have = wk.x;
-            __syncthreads();
+    int w = blockIdx.x;
+    if (w >= nwork) return;
+    int2 wk = work[w];
+    if (STG == 2) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(insts[wk.x], wk.y, s0);
+    for (int i = 0; w < nwork; ++i, w += gridDim.x) {
+        const Inst& I = insts[wk.x];
+        T* const cur = (i & 1) ? s1 : s0;
+        if (STG == 1) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, wk.y, cur);
+        if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, wk.y, tr);
+        const int wn = w + gridDim.x;
+        int2 wkn = wk;
+        if (wn < nwork) wkn = work[wn];
+        if (STG == 2 && wn < nwork) {
+            fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(insts[wkn.x], wkn.y, (i & 1) ? s0 : s1);
+            cp_wait_prior();
+        } else {
+            cp_wait_all();
         }
-        fixed_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(Ish, wk.y, s, tr);
+        __syncthreads();
+        fixed_compute<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, wk.y, cur, tr);
+        wk = wkn;
     }
 }
 

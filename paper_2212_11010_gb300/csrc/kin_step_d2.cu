@@ -14,23 +14,29 @@ static StepKernel pick(int prec)
 }
 
 
-// Fixed shapes compiled for 2D: (degree, system, precision, B0, B1, threads, min blocks per SM).
-#define KIN_FIXED_2D(X)                        \
-    X(1, kEuler, float, 16, 8, 128, 6)         \
-    X(2, kEuler, float, 8, 8, 192, 5)          \
-    X(3, kEuler, float, 8, 4, 128, 6)          \
-    X(2, kEuler, double, 8, 8, 192, 3)
+// Fixed shapes compiled for 2D: (degree, system, precision, B0, B1, threads,
+// min blocks per SM with one tile buffer, with two tile buffers).
+#define KIN_FIXED_2D(X)                           \
+    X(1, kEuler, float, 16, 8, 128, 6, 3)         \
+    X(2, kEuler, float, 8, 8, 192, 5, 3)          \
+    X(3, kEuler, float, 8, 4, 128, 6, 3)          \
+    X(2, kEuler, double, 8, 8, 192, 3, 1)
 
-FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3])
+FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3], int stages)
 {
     FixedKernel k{nullptr, nullptr, 0, 0};
-#define KIN_TRY(PP, SY, TT, X0, X1, NT, MB)                                                        \
+#define KIN_TRY(PP, SY, TT, X0, X1, NT, MB1, MB2)                                                  \
     if (degree == PP && system == SY && prec == (sizeof(TT) == 4 ? 1 : 0) && B[0] == X0 && B[1] == X1 && \
         B[2] == 1) {                                                                                \
-        k.fn = (StepKernel)step_kernel_fixed<2, PP, SY, TT, X0, X1, 1, NT, MB>;                       \
-        k.batch_fn = (const void*)step_kernel_fixed_batch<2, PP, SY, TT, X0, X1, 1, NT, MB>;          \
+        if (stages == 2) {                                                                          \
+            k.fn = (StepKernel)step_kernel_fixed<2, PP, SY, TT, X0, X1, 1, NT, MB2, 2>;               \
+            k.batch_fn = (const void*)step_kernel_fixed_batch<2, PP, SY, TT, X0, X1, 1, NT, MB2, 2>;  \
+        } else {                                                                                    \
+            k.fn = (StepKernel)step_kernel_fixed<2, PP, SY, TT, X0, X1, 1, NT, MB1, 1>;               \
+            k.batch_fn = (const void*)step_kernel_fixed_batch<2, PP, SY, TT, X0, X1, 1, NT, MB1, 1>;  \
+        }                                                                                           \
         k.threads = NT;                                                                             \
-        k.smem = Shape<2, PP, SY, TT, X0, X1, 1>::SMEM;                                              \
+        k.smem = (stages == 2 ? 2 : 1) * Shape<2, PP, SY, TT, X0, X1, 1>::SMEM;                      \
         return k;                                                                                   \
     }
     KIN_FIXED_2D(KIN_TRY)

@@ -14,29 +14,40 @@ static StepKernel pick(int prec)
 }
 
 
-// Fixed shapes compiled for 3D: (degree, system, precision, B0, B1, B2, threads, min blocks per SM).
-#define KIN_FIXED_3D(X)                          \
-    X(1, kEuler, float, 8, 2, 2, 128, 6)         \
-    X(1, kEuler, float, 4, 4, 2, 128, 6)         \
-    X(1, kEuler, float, 8, 4, 2, 256, 3)         \
-    X(1, kEuler, float, 4, 4, 4, 320, 3)
+// Fixed shapes compiled for 3D: (degree, system, precision, B0, B1, B2,
+// threads, min blocks per SM with one tile buffer, with two tile buffers).
+#define KIN_FIXED_3D(X)                             \
+    X(1, kEuler, float, 8, 2, 2, 128, 6, 3)         \
+    X(1, kEuler, float, 4, 4, 2, 128, 6, 3)         \
+    X(1, kEuler, float, 8, 4, 2, 256, 3, 1)         \
+    X(1, kEuler, float, 4, 4, 4, 320, 3, 1)
 
-FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3])
+FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3], int stages)
 {
     FixedKernel k{nullptr, nullptr, 0, 0};
-#define KIN_TRY(PP, SY, TT, X0, X1, X2, NT, MB)                                                    \
+#define KIN_TRY(PP, SY, TT, X0, X1, X2, NT, MB1, MB2)                                              \
     if (degree == PP && system == SY && prec == (sizeof(TT) == 4 ? 1 : 0) && B[0] == X0 && B[1] == X1 && \
         B[2] == X2) {                                                                               \
-        k.fn = (StepKernel)step_kernel_fixed<3, PP, SY, TT, X0, X1, X2, NT, MB>;                      \
-        k.batch_fn = (const void*)step_kernel_fixed_batch<3, PP, SY, TT, X0, X1, X2, NT, MB>;         \
+        if (stages == 2) {                                                                          \
+            k.fn = (StepKernel)step_kernel_fixed<3, PP, SY, TT, X0, X1, X2, NT, MB2, 2>;              \
+            k.batch_fn = (const void*)step_kernel_fixed_batch<3, PP, SY, TT, X0, X1, X2, NT, MB2, 2>; \
+        } else {                                                                                    \
+            k.fn = (StepKernel)step_kernel_fixed<3, PP, SY, TT, X0, X1, X2, NT, MB1, 1>;              \
+            k.batch_fn = (const void*)step_kernel_fixed_batch<3, PP, SY, TT, X0, X1, X2, NT, MB1, 1>; \
+        }                                                                                           \
         k.threads = NT;                                                                             \
-        k.smem = Shape<3, PP, SY, TT, X0, X1, X2>::SMEM;                                             \
+        k.smem = (stages == 2 ? 2 : 1) * Shape<3, PP, SY, TT, X0, X1, X2>::SMEM;                     \
         return k;                                                                                   \
     }
     KIN_FIXED_3D(KIN_TRY)
 #undef KIN_TRY
     return k;
 }
+
+// One tile buffer: the two-buffer schedule halves the resident blocks, and
+// with the look-back folded while the copies fly the loads are already hidden
+// behind the other blocks' work (measured slower for every compiled shape).
+int fixed_default_stages(int, int, int, int, const int*) { return 1; }
 
 int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3])
 {

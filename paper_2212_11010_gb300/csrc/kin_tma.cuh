@@ -140,5 +140,7 @@ __device__ __forceinline__ void cp16_g2s(void* sdst, const void* gsrc)
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// all but the most recent commit group of this thread have landed
+__device__ __forceinline__ void cp_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 }  // namespace kin

@@ -37,8 +37,8 @@ def _problem(dim, degree, prec, block):
     return workloads.with_(w, tiles=(2, 2, 2))
 
 
-def _run(kin, w, block, steps, threads=0):
-    with kin.Context.from_workload(w, block=block, threads=threads) as ctx:
+def _run(kin, w, block, steps, threads=0, stages=0):
+    with kin.Context.from_workload(w, block=block, threads=threads, stages=stages) as ctx:
         ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
         ctx.step(steps)
         return ctx.get_state(), ctx.get_kinetic(), ctx.info
@@ -69,3 +69,19 @@ def test_default_block_uses_fixed_kernel_for_benchmarked_workload(kin):
     with kin.Context.from_workload(w) as ctx:
         assert ctx.info.specialised == 1
         assert tuple(ctx.info.block[:2]) == (8, 8)
+
+
+TWO_BUFFER = [(2, 2, "f32", (8, 8)), (2, 1, "f32", (16, 8)), (3, 1, "f32", (4, 4, 2))]
+
+
+@pytest.mark.parametrize("shape", TWO_BUFFER, ids=[str(s) for s in TWO_BUFFER])
+def test_two_buffer_schedule_is_bitwise_identical(kin, shape):
+    """The two-buffer schedule changes only when tiles are loaded, not what
+    any thread computes: the state after several steps is bit for bit the
+    one-buffer result."""
+    dim, degree, prec, block = shape
+    w = _problem(dim, degree, prec, block)
+    _, f1, i1 = _run(kin, w, block, 3, stages=1)
+    _, f2, i2 = _run(kin, w, block, 3, stages=2)
+    assert (i1.stages, i2.stages) == (1, 2) and i1.specialised == 1 and i2.specialised == 1
+    assert np.array_equal(f1, f2)
