@@ -128,6 +128,14 @@ struct Shape {
     static constexpr int PSTR = pstr(RP, PP);
     static constexpr int TILE = NPOP * PSTR;                        // elements per tile buffer
     static constexpr size_t SMEM = sizeof(T) * (size_t)TILE;
+    // line items of the tile, axis by axis: (variable, line) pairs; each
+    // item stands for the + and the - population of its line
+    static constexpr int E0 = M * lines(0);
+    static constexpr int E1 = E0 + (D > 1 ? M * lines(1) : 0);
+    static constexpr int ITEMS = E1 + (D > 2 ? M * lines(2) : 0);
+    static constexpr int eoff(int a) { return a == 0 ? 0 : (a == 1 ? E0 : E1); }
+    // inflow traces of the tile (shared memory after the tile buffers): [sign][item]
+    static constexpr size_t TIN_BYTES = sizeof(T) * (size_t)(((2 * ITEMS * sizeof(T) + 15) / 16) * 16 / sizeof(T));
     // lines of one sign of axis a handled by each thread of a sign half
     static constexpr int kpt(int a, int half) { return (M * lines(a) + half - 1) / half; }
     static constexpr int kpt_max(int half)
@@ -161,92 +169,200 @@ __device__ __forceinline__ long long fixed_gline(const Inst& I, int line, int or
     return gt * TN + tnode;
 }
 
-// One half of the threads handles the lines of velocity sign SGN of axis A;
-// thread 'hid' of the half owns items hid, hid + HALF, ...  The look-back
-// inflows of those items live in the registers tr[] (same item order).
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int A, int SGN, int MODE>
-__device__ __forceinline__ void fixed_lines(const Inst& I, int hid, int org0, int org1, int org2, int bidx,
-                                            T* s, T* tr)
+// Pair arithmetic for the + and - population of one line: FP32 pairs are
+// packed instructions (each lane the scalar IEEE operation of the same
+// name), FP64 pairs two scalar operations.
+template <typename T>
+struct PairOf;
+template <>
+struct PairOf<float> {
+    using type = float2;
+};
+template <>
+struct PairOf<double> {
+    using type = double2;
+};
+__device__ __forceinline__ float2 pmk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 pmk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+
+// Coefficient k of direction dir: from the launch parameters (one problem
+// per launch), or for batched launches from a shared-memory copy when one is
+// given, else from the instance's launch record in global memory.
+template <bool BATCH, typename T>
+__device__ __forceinline__ T cget(const Inst& I, const T* csm, int dir, int k)
+{
+    if constexpr (BATCH)
+        return csm ? csm[dir * kCoefStride + k] : coef_of(I, dir, k, T(0));
+    else
+        return coef_of(I, dir, k, T(0));
+}
+
+// Sweep (MODE 1) or block summaries (MODE 2) of one line item of axis A:
+// variable v, line 'line'; the + population sweeps the cells upward in lane
+// x and the - population downward in lane y.  The look-back inflows come from
+// tin[sign][item].
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int A, int MODE, bool BATCH>
+__device__ __forceinline__ void pm_item(const Inst& I, int local, int org0, int org1, int org2, int bidx, T* s,
+                                        const T* tin, const T* csm)
 {
     using S = Shape<D, P, SYS, T, B0, B1, B2>;
-    constexpr int NP = S::NP, M = S::M, HALF = NTH / 2;
-    constexpr int LP = S::lines(A);
-    constexpr int ITEMS = M * LP;                   // items of this sign
-    constexpr int KPT = S::kpt(A, HALF);
-    constexpr int BA = S::ext(A);
-    constexpr int CST = S::cstep(S::RP, A);
-    constexpr int NS = S::nstep(A);
-    constexpr int DIR = 2 * A + SGN;
-
+    using T2 = typename PairOf<T>::type;
+    constexpr int NP = S::NP, M = S::M, LP = S::lines(A), BA = S::ext(A);
+    constexpr int CST = S::cstep(S::RP, A), NS = S::nstep(A);
+    const int v = local / LP, line = local - (local / LP) * LP;
+    const int popP = (2 * A) * M + v;
+    T* const sp = s + S::line_base(S::RP, S::PP, A, popP, line);     // + population
+    T* const sm = sp + M * S::PSTR;                                    // - population (pop + M)
+    if constexpr (BATCH) {
+        // launch records in global memory: the two directions one after the
+        // other in scalar arithmetic, each coefficient read where it is used
+        // (a packed pair would hold every coefficient pair in registers)
+#pragma unroll
+        for (int sg = 0; sg < 2; ++sg) {
+            const int dir = 2 * A + sg;
+            T* const base = sg == 0 ? sp : sm;
+            if (MODE == 1) {
+                T t = tin[sg * S::ITEMS + S::eoff(A) + local];
+#pragma unroll
+                for (int cc = 0; cc < BA; ++cc) {
+                    T* const p = base + (sg == 0 ? cc : BA - 1 - cc) * CST;
+                    T u[NP], dlt[NP];
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) u[j] = p[j * NS];
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) {
+                        T acc = cget<true>(I, csm, dir, i * NP) * u[0];
+#pragma unroll
+                        for (int j = 1; j < NP; ++j) acc = fma(cget<true>(I, csm, dir, i * NP + j), u[j], acc);
+                        dlt[i] = fma(cget<true>(I, csm, dir, kOffG + i), t, acc);
+                    }
+                    t = sg == 0 ? u[NP - 1] + dlt[NP - 1] : u[0] + dlt[0];
+#pragma unroll
+                    for (int i = 0; i < NP; ++i) p[i * NS] = fma(T(2), dlt[i], u[i]);
+                }
+            } else {
+                const T rho = cget<true>(I, csm, dir, kOffRho);
+                T t = 0;
+#pragma unroll
+                for (int cc = 0; cc < BA; ++cc) {
+                    const T* const p = base + (sg == 0 ? cc : BA - 1 - cc) * CST;
+                    T acc = cget<true>(I, csm, dir, kOffProw) * p[0];
+#pragma unroll
+                    for (int j = 1; j < NP; ++j) acc = fma(cget<true>(I, csm, dir, kOffProw + j), p[j * NS], acc);
+                    t = fma(rho, t, acc);
+                }
+                const T last = sg == 0 ? sp[(BA - 1) * CST + (NP - 1) * NS] : sm[0];
+                const int nbk = I.nblk[A], nbs = I.nb[A];
+                const int q = sg == 0 ? bidx : nbk - 1 - bidx;
+                const int Sd = (int)fdiv((unsigned)q, I.fd_nb[A]);
+                const long long gl = I.ax[A].glines;
+                const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
+                const int pop = popP + sg * M;
+                static_cast<T*>(I.sig_out)[(long long)pop * I.sig_stride + (long long)q * gl + gline] = t;
+                if (q - Sd * nbs == nbs - 1)
+                    static_cast<T*>(I.raw_out)[(long long)pop * I.raw_stride + (long long)Sd * gl + gline] = last;
+            }
+        }
+        return;
+    }
     if (MODE == 1) {
-        T Pm[NP][NP], g[NP];
+        T2 Pm[NP][NP], g[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            g[i] = coef_of(I, DIR, kOffG + i, T(0));
+            g[i] = pmk(cget<BATCH>(I, csm, 2 * A, kOffG + i), cget<BATCH>(I, csm, 2 * A + 1, kOffG + i));
 #pragma unroll
-            for (int j = 0; j < NP; ++j) Pm[i][j] = coef_of(I, DIR, i * NP + j, T(0));
+            for (int j = 0; j < NP; ++j)
+                Pm[i][j] = pmk(cget<BATCH>(I, csm, 2 * A, i * NP + j), cget<BATCH>(I, csm, 2 * A + 1, i * NP + j));
         }
+        T2 t = pmk(tin[S::eoff(A) + local], tin[S::ITEMS + S::eoff(A) + local]);
+        const T2 two = pmk(T(2), T(2));
 #pragma unroll
-        for (int k = 0; k < KPT; ++k) {
-            const int it = hid + k * HALF;
-            if (ITEMS % HALF != 0 && it >= ITEMS) break;
-            const int v = it / LP, line = it % LP;
-            const int pop = (2 * A + SGN) * M + v;
-            const int base = S::line_base(S::RP, S::PP, A, pop, line);
-            T t = tr[k];
+        for (int cc = 0; cc < BA; ++cc) {
+            T* const p = sp + cc * CST;
+            T* const m = sm + (BA - 1 - cc) * CST;
+            T2 u[NP], dlt[NP];
 #pragma unroll
-            for (int cc = 0; cc < BA; ++cc) {
-                T* p = s + base + (SGN == 0 ? cc : BA - 1 - cc) * CST;
-                T u[NP], dlt[NP];
+            for (int j = 0; j < NP; ++j) u[j] = pmk(p[j * NS], m[j * NS]);
 #pragma unroll
-                for (int j = 0; j < NP; ++j) u[j] = p[j * NS];
+            for (int i = 0; i < NP; ++i) {
+                T2 acc = pmul(Pm[i][0], u[0]);
 #pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    T acc = Pm[i][0] * u[0];
+                for (int j = 1; j < NP; ++j) acc = pfma(Pm[i][j], u[j], acc);
+                dlt[i] = pfma(g[i], t, acc);        // f* - f^n at node i
+            }
+            // outflow traces: node p of the + line, node 0 of the - line
+            t = pmk(u[NP - 1].x + dlt[NP - 1].x, u[0].y + dlt[0].y);
 #pragma unroll
-                    for (int j = 1; j < NP; ++j) acc = fma(Pm[i][j], u[j], acc);
-                    dlt[i] = fma(g[i], t, acc);
-                }
-                t = SGN == 0 ? u[NP - 1] + dlt[NP - 1] : u[0] + dlt[0];
-#pragma unroll
-                for (int i = 0; i < NP; ++i) p[i * NS] = fma(T(2), dlt[i], u[i]);
+            for (int i = 0; i < NP; ++i) {
+                const T2 nw = pfma(two, dlt[i], u[i]);
+                p[i * NS] = nw.x;
+                m[i * NS] = nw.y;
             }
         }
     } else {
-        T prow[NP];
+        T2 prow[NP];
 #pragma unroll
-        for (int j = 0; j < NP; ++j) prow[j] = coef_of(I, DIR, kOffProw + j, T(0));
-        const T rho = coef_of(I, DIR, kOffRho, T(0));
+        for (int j = 0; j < NP; ++j)
+            prow[j] = pmk(cget<BATCH>(I, csm, 2 * A, kOffProw + j), cget<BATCH>(I, csm, 2 * A + 1, kOffProw + j));
+        const T2 rho = pmk(cget<BATCH>(I, csm, 2 * A, kOffRho), cget<BATCH>(I, csm, 2 * A + 1, kOffRho));
+        T2 t = pmk(T(0), T(0));
+#pragma unroll
+        for (int cc = 0; cc < BA; ++cc) {
+            const T* const p = sp + cc * CST;
+            const T* const m = sm + (BA - 1 - cc) * CST;
+            T2 u[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) u[j] = pmk(p[j * NS], m[j * NS]);
+            T2 acc = pmul(prow[0], u[0]);
+#pragma unroll
+            for (int j = 1; j < NP; ++j) acc = pfma(prow[j], u[j], acc);
+            t = pfma(rho, t, acc);
+        }
+        // the outflow-node values of f (the last cell of each direction)
+        const T lastP = sp[(BA - 1) * CST + (NP - 1) * NS];
+        const T lastM = sm[0];
         const int nbk = I.nblk[A], nbs = I.nb[A];
-        const int q = SGN == 0 ? bidx : nbk - 1 - bidx;
-        const int Sd = q / nbs;
-        const bool writes_raw = q - Sd * nbs == nbs - 1;    // downwind-most block of its subdomain
         const long long gl = I.ax[A].glines;
-        T* __restrict__ sig = static_cast<T*>(I.sig_out) + (long long)q * gl;
-        T* __restrict__ raw = static_cast<T*>(I.raw_out) + (long long)Sd * gl;
+        const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
+        T* __restrict__ sig = static_cast<T*>(I.sig_out);
+        T* __restrict__ raw = static_cast<T*>(I.raw_out);
 #pragma unroll
-        for (int k = 0; k < KPT; ++k) {
-            const int it = hid + k * HALF;
-            if (ITEMS % HALF != 0 && it >= ITEMS) break;
-            const int v = it / LP, line = it % LP;
-            const int pop = (2 * A + SGN) * M + v;
-            const int base = S::line_base(S::RP, S::PP, A, pop, line);
-            T t = 0, last = 0;
+        for (int sg = 0; sg < 2; ++sg) {
+            const int q = sg == 0 ? bidx : nbk - 1 - bidx;
+            const int Sd = (int)fdiv((unsigned)q, I.fd_nb[A]);
+            const int pop = popP + sg * M;
+            sig[(long long)pop * I.sig_stride + (long long)q * gl + gline] = sg == 0 ? t.x : t.y;
+            if (q - Sd * nbs == nbs - 1)     // downwind-most block of its subdomain
+                raw[(long long)pop * I.raw_stride + (long long)Sd * gl + gline] = sg == 0 ? lastP : lastM;
+        }
+    }
+}
+
+// Every line item of the tile, axis after axis, spread over all threads
+// (items it, it + NTH, ...).  Axis boundaries fall on warp boundaries for
+// the compiled shapes, so the axis branch does not split a warp.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MODE, bool BATCH>
+__device__ __forceinline__ void fixed_pm_all(const Inst& I, int org0, int org1, int org2, int bx, int by, int bz,
+                                             T* s, const T* tin, const T* csm)
+{
+    using S = Shape<D, P, SYS, T, B0, B1, B2>;
 #pragma unroll
-            for (int cc = 0; cc < BA; ++cc) {
-                const T* p = s + base + (SGN == 0 ? cc : BA - 1 - cc) * CST;
-                T u[NP];
-#pragma unroll
-                for (int j = 0; j < NP; ++j) u[j] = p[j * NS];
-                T acc = prow[0] * u[0];
-#pragma unroll
-                for (int j = 1; j < NP; ++j) acc = fma(prow[j], u[j], acc);
-                t = fma(rho, t, acc);
-                last = SGN == 0 ? u[NP - 1] : u[0];
-            }
-            const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
-            sig[(long long)pop * I.sig_stride + gline] = t;
-            if (writes_raw) raw[(long long)pop * I.raw_stride + gline] = last;
+    for (int k = 0; k < (S::ITEMS + NTH - 1) / NTH; ++k) {
+        const int it = threadIdx.x + k * NTH;
+        if (S::ITEMS % NTH != 0 && it >= S::ITEMS) break;
+        if (it < S::E0) {
+            pm_item<D, P, SYS, T, B0, B1, B2, 0, MODE, BATCH>(I, it, org0, org1, org2, bx, s, tin, csm);
+        } else if (D == 2 || it < S::E1) {
+            if constexpr (D > 1) pm_item<D, P, SYS, T, B0, B1, B2, 1, MODE, BATCH>(I, it - S::E0, org0, org1, org2, by, s, tin, csm);
+        } else {
+            if constexpr (D > 2) pm_item<D, P, SYS, T, B0, B1, B2, 2, MODE, BATCH>(I, it - S::E1, org0, org1, org2, bz, s, tin, csm);
         }
     }
 }
@@ -298,12 +414,14 @@ __device__ __forceinline__ void chain_setup(const Inst& I, int hid, int sgn, int
 // index of its next summary, which moves by the line count of its axis and
 // wraps (periodically) after the last block; the unrolled steps let the
 // loads of several steps be in flight at once.
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH>
 __device__ __forceinline__ void fixed_chain(const Inst& I, int org0, int org1, int org2, int bx, int by, int bz,
-                                            T (&tr)[3][KM])
+                                            T* tin)
 {
     using S = Shape<D, P, SYS, T, B0, B1, B2>;
     constexpr int HALF = NTH / 2;
+    constexpr int KM = S::kpt_max(HALF);
+    T tr[3][KM];
     constexpr int KP[3] = {S::kpt(0, HALF), D > 1 ? S::kpt(1, HALF) : 0, D > 2 ? S::kpt(2, HALF) : 0};
     const int tid = threadIdx.x;
     const int sgn = tid < HALF ? 0 : 1;
@@ -349,25 +467,14 @@ __device__ __forceinline__ void fixed_chain(const Inst& I, int org0, int org1, i
             }
         }
     }
-}
-
-// MODE 1: transport sweeps, 2: block summaries.  Each sign half runs its
-// own warps (HALF is a multiple of 32).
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MODE, int KM>
-__device__ __forceinline__ void fixed_lines_all(const Inst& I, int org0, int org1, int org2, int bx, int by,
-                                                int bz, T* s, T (&tr)[3][KM])
-{
-    const int tid = threadIdx.x;
-    const int hid = tid < NTH / 2 ? tid : tid - NTH / 2;
-    if (tid < NTH / 2) {
-        fixed_lines<D, P, SYS, T, B0, B1, B2, NTH, 0, 0, MODE>(I, hid, org0, org1, org2, bx, s, tr[0]);
-        if constexpr (D > 1) fixed_lines<D, P, SYS, T, B0, B1, B2, NTH, 1, 0, MODE>(I, hid, org0, org1, org2, by, s, tr[1]);
-        if constexpr (D > 2) fixed_lines<D, P, SYS, T, B0, B1, B2, NTH, 2, 0, MODE>(I, hid, org0, org1, org2, bz, s, tr[2]);
-    } else {
-        fixed_lines<D, P, SYS, T, B0, B1, B2, NTH, 0, 1, MODE>(I, hid, org0, org1, org2, bx, s, tr[0]);
-        if constexpr (D > 1) fixed_lines<D, P, SYS, T, B0, B1, B2, NTH, 1, 1, MODE>(I, hid, org0, org1, org2, by, s, tr[1]);
-        if constexpr (D > 2) fixed_lines<D, P, SYS, T, B0, B1, B2, NTH, 2, 1, MODE>(I, hid, org0, org1, org2, bz, s, tr[2]);
-    }
+    // tin[sign][item]; item = offset of the axis + (variable, line) index
+#pragma unroll
+    for (int A = 0; A < D; ++A)
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const int it = hid + k * HALF;
+            if (k < KP[A] && it < S::M * S::lines(A)) tin[sgn * S::ITEMS + S::eoff(A) + it] = tr[A][k];
+        }
 }
 
 template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH>
@@ -597,13 +704,13 @@ __device__ __forceinline__ void fixed_copy(const Inst& I, int org0, int org1, in
 // The work of one tile once its data is in shared memory: sweep, relax,
 // store, write the summaries, and meet at a barrier before the buffer is
 // reused.
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
-__device__ __forceinline__ void fixed_compute(const Inst& I, int t, T* s, T (&tr)[3][KM])
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, bool BATCH>
+__device__ __forceinline__ void fixed_compute(const Inst& I, int t, T* s, const T* tin, const T* csm)
 {
     const TileXYZ c = tile_xyz(I, t);
     const int org0 = c.bx * B0, org1 = c.by * B1, org2 = c.bz * B2;
     if (I.mode == 0) {
-        fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 1, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
+        fixed_pm_all<D, P, SYS, T, B0, B1, B2, NTH, 1, BATCH>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tin, csm);
         __syncthreads();
         if constexpr (std::is_same<T, float>::value && Shape<D, P, SYS, T, B0, B1, B2>::ROWLEN % 2 == 0)
             fixed_relax_pairs<D, P, SYS, B0, B1, B2, NTH>(I, s);
@@ -612,7 +719,7 @@ __device__ __forceinline__ void fixed_compute(const Inst& I, int t, T* s, T (&tr
         __syncthreads();
         fixed_copy<D, P, SYS, T, B0, B1, B2, NTH, true>(I, org0, org1, org2, s);
     }
-    fixed_lines_all<D, P, SYS, T, B0, B1, B2, NTH, 2, KM>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tr);
+    fixed_pm_all<D, P, SYS, T, B0, B1, B2, NTH, 2, BATCH>(I, org0, org1, org2, c.bx, c.by, c.bz, s, tin, csm);
     __syncthreads();
 }
 
@@ -623,11 +730,11 @@ __device__ __forceinline__ void fixed_load(const Inst& I, int t, T* s)
     fixed_copy<D, P, SYS, T, B0, B1, B2, NTH, false>(I, c.bx * B0, c.by * B1, c.bz * B2, s);
 }
 
-template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int KM>
-__device__ __forceinline__ void fixed_chain_tile(const Inst& I, int t, T (&tr)[3][KM])
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH>
+__device__ __forceinline__ void fixed_chain_tile(const Inst& I, int t, T* tin)
 {
     const TileXYZ c = tile_xyz(I, t);
-    fixed_chain<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, c.bx * B0, c.by * B1, c.bz * B2, c.bx, c.by, c.bz, tr);
+    fixed_chain<D, P, SYS, T, B0, B1, B2, NTH>(I, c.bx * B0, c.by * B1, c.bz * B2, c.bx, c.by, c.bz, tin);
 }
 
 // Fixed-shape step kernel on a persistent grid (blocks walk tiles
@@ -643,8 +750,7 @@ __global__ void __launch_bounds__(NTH, MINB) step_kernel_fixed(const __grid_cons
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* const s0 = reinterpret_cast<T*>(smem_raw);
     T* const s1 = s0 + (STG == 2 ? S::TILE : 0);
-    constexpr int KM = S::kpt_max(NTH / 2);
-    T tr[3][KM];      // look-back inflows of this thread's lines
+    T* const tin = s0 + STG * S::TILE;       // look-back inflows of the current tile
     const int ntiles = I.nblk[0] * I.nblk[1] * I.nblk[2];
     int t = blockIdx.x;
     if (t >= ntiles) return;
@@ -652,7 +758,7 @@ __global__ void __launch_bounds__(NTH, MINB) step_kernel_fixed(const __grid_cons
     for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
         T* const cur = (i & 1) ? s1 : s0;
         if (STG == 1) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, t, cur);
-        if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, t, tr);
+        if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH>(I, t, tin);
         const int tn = t + gridDim.x;
         if (STG == 2 && tn < ntiles) {
             fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, tn, (i & 1) ? s0 : s1);
@@ -661,14 +767,14 @@ __global__ void __launch_bounds__(NTH, MINB) step_kernel_fixed(const __grid_cons
             cp_wait_all();
         }
         __syncthreads();
-        fixed_compute<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, t, cur, tr);
+        fixed_compute<D, P, SYS, T, B0, B1, B2, NTH, false>(I, t, cur, tin, nullptr);
     }
 }
 
 // Batched fixed-shape step kernel: the thread blocks walk a work list of
 // (instance, tile) pairs over several independent problems of the same
-// kernel type, reading each instance's launch record from global memory
-// (read-only for the launch), with the same one- or two-buffer schedule.
+// kernel type, with the same one- or two-buffer schedule.  Launch records
+// are read from global memory (read-only for the launch).
 template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MINB, int STG>
 __global__ void __launch_bounds__(NTH, MINB)
     step_kernel_fixed_batch(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork)
@@ -677,8 +783,7 @@ __global__ void __launch_bounds__(NTH, MINB)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* const s0 = reinterpret_cast<T*>(smem_raw);
     T* const s1 = s0 + (STG == 2 ? S::TILE : 0);
-    constexpr int KM = S::kpt_max(NTH / 2);
-    T tr[3][KM];
+    T* const tin = s0 + STG * S::TILE;
     int w = blockIdx.x;
     if (w >= nwork) return;
     int2 wk = work[w];
@@ -687,7 +792,7 @@ __global__ void __launch_bounds__(NTH, MINB)
         const Inst& I = insts[wk.x];
         T* const cur = (i & 1) ? s1 : s0;
         if (STG == 1) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, wk.y, cur);
-        if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, wk.y, tr);
+        if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH>(I, wk.y, tin);
         const int wn = w + gridDim.x;
         int2 wkn = wk;
         if (wn < nwork) wkn = work[wn];
@@ -698,7 +803,7 @@ __global__ void __launch_bounds__(NTH, MINB)
             cp_wait_all();
         }
         __syncthreads();
-        fixed_compute<D, P, SYS, T, B0, B1, B2, NTH, KM>(I, wk.y, cur, tr);
+        fixed_compute<D, P, SYS, T, B0, B1, B2, NTH, true>(I, wk.y, cur, tin, nullptr);
         wk = wkn;
     }
 }

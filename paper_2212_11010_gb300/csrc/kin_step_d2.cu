@@ -36,7 +36,8 @@ FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3], in
             k.batch_fn = (const void*)step_kernel_fixed_batch<2, PP, SY, TT, X0, X1, 1, NT, MB1, 1>;  \
         }                                                                                           \
         k.threads = NT;                                                                             \
-        k.smem = (stages == 2 ? 2 : 1) * Shape<2, PP, SY, TT, X0, X1, 1>::SMEM;                      \
+        k.smem = (stages == 2 ? 2 : 1) * Shape<2, PP, SY, TT, X0, X1, 1>::SMEM +                    \
+                 Shape<2, PP, SY, TT, X0, X1, 1>::TIN_BYTES;                                          \
         return k;                                                                                   \
     }
     KIN_FIXED_2D(KIN_TRY)

@@ -36,7 +36,8 @@ FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3], in
             k.batch_fn = (const void*)step_kernel_fixed_batch<3, PP, SY, TT, X0, X1, X2, NT, MB1, 1>; \
         }                                                                                           \
         k.threads = NT;                                                                             \
-        k.smem = (stages == 2 ? 2 : 1) * Shape<3, PP, SY, TT, X0, X1, X2>::SMEM;                     \
+        k.smem = (stages == 2 ? 2 : 1) * Shape<3, PP, SY, TT, X0, X1, X2>::SMEM +                   \
+                 Shape<3, PP, SY, TT, X0, X1, X2>::TIN_BYTES;                                         \
         return k;                                                                                   \
     }
     KIN_FIXED_3D(KIN_TRY)
@@ -68,10 +69,10 @@ int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3])
     }
     if (dim == 2 && prec == 0 && degree == 2) add(8, 8, 1);
     if (dim == 3 && prec == 1 && degree == 1) {
-        add(4, 4, 2);
         add(4, 4, 4);
-        add(8, 2, 2);
         add(8, 4, 2);
+        add(4, 4, 2);
+        add(8, 2, 2);
     }
     return n;
 }
