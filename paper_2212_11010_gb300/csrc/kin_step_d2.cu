@@ -18,8 +18,10 @@ static StepKernel pick(int prec)
 // min blocks per SM with one tile buffer, with two tile buffers).
 #define KIN_FIXED_2D(X)                           \
     X(1, kEuler, float, 16, 8, 128, 6, 3)         \
+    X(1, kEuler, float, 16, 16, 256, 3, 1)        \
     X(2, kEuler, float, 8, 8, 192, 5, 3)          \
     X(3, kEuler, float, 8, 4, 128, 6, 3)          \
+    X(3, kEuler, float, 8, 8, 256, 3, 1)          \
     X(2, kEuler, double, 8, 8, 192, 3, 1)
 
 FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3], int stages)

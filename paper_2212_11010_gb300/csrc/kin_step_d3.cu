@@ -63,9 +63,15 @@ int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3])
     };
     if (system != kEuler) return 0;
     if (dim == 2 && prec == 1) {
-        if (degree == 1) add(16, 8, 1);
+        if (degree == 1) {
+            add(16, 16, 1);
+            add(16, 8, 1);
+        }
         if (degree == 2) add(8, 8, 1);
-        if (degree == 3) add(8, 4, 1);
+        if (degree == 3) {
+            add(8, 8, 1);
+            add(8, 4, 1);
+        }
     }
     if (dim == 2 && prec == 0 && degree == 2) add(8, 8, 1);
     if (dim == 3 && prec == 1 && degree == 1) {

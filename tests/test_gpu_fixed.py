@@ -11,7 +11,8 @@ pytestmark = pytest.mark.gpu
 
 # (dim, degree, precision, block) of every compiled fixed shape
 SHAPES = [
-    (2, 1, "f32", (16, 8)), (2, 2, "f32", (8, 8)), (2, 3, "f32", (8, 4)), (2, 2, "f64", (8, 8)),
+    (2, 1, "f32", (16, 8)), (2, 1, "f32", (16, 16)), (2, 2, "f32", (8, 8)), (2, 3, "f32", (8, 4)),
+    (2, 3, "f32", (8, 8)), (2, 2, "f64", (8, 8)),
     (3, 1, "f32", (8, 2, 2)), (3, 1, "f32", (4, 4, 2)), (3, 1, "f32", (8, 4, 2)), (3, 1, "f32", (4, 4, 4)),
 ]
 
