@@ -169,29 +169,6 @@ __device__ __forceinline__ long long fixed_gline(const Inst& I, int line, int or
     return gt * TN + tnode;
 }
 
-// Pair arithmetic for the + and - population of one line: FP32 pairs are
-// packed instructions (each lane the scalar IEEE operation of the same
-// name), FP64 pairs two scalar operations.
-template <typename T>
-struct PairOf;
-template <>
-struct PairOf<float> {
-    using type = float2;
-};
-template <>
-struct PairOf<double> {
-    using type = double2;
-};
-__device__ __forceinline__ float2 pmk(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ double2 pmk(double a, double b) { return make_double2(a, b); }
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
-{
-    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
-
 // Coefficient k of direction dir: from the launch parameters (one problem
 // per launch), or for batched launches from a shared-memory copy when one is
 // given, else from the instance's launch record in global memory.
@@ -205,142 +182,66 @@ __device__ __forceinline__ T cget(const Inst& I, const T* csm, int dir, int k)
 }
 
 // Sweep (MODE 1) or block summaries (MODE 2) of one line item of axis A:
-// variable v, line 'line'; the + population sweeps the cells upward in lane
-// x and the - population downward in lane y.  The look-back inflows come from
-// tin[sign][item].
+// variable v, line 'line', for both velocity signs of the axis.  The
+// look-back inflows come from tin[sign][item].
 template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int A, int MODE, bool BATCH>
 __device__ __forceinline__ void pm_item(const Inst& I, int local, int org0, int org1, int org2, int bidx, T* s,
                                         const T* tin, const T* csm)
 {
     using S = Shape<D, P, SYS, T, B0, B1, B2>;
-    using T2 = typename PairOf<T>::type;
     constexpr int NP = S::NP, M = S::M, LP = S::lines(A), BA = S::ext(A);
     constexpr int CST = S::cstep(S::RP, A), NS = S::nstep(A);
     const int v = local / LP, line = local - (local / LP) * LP;
     const int popP = (2 * A) * M + v;
     T* const sp = s + S::line_base(S::RP, S::PP, A, popP, line);     // + population
     T* const sm = sp + M * S::PSTR;                                    // - population (pop + M)
-    if constexpr (BATCH) {
-        // launch records in global memory: the two directions one after the
-        // other in scalar arithmetic, each coefficient read where it is used
-        // (a packed pair would hold every coefficient pair in registers)
+    // the two directions one after the other: the + line upward, then the -
+    // line downward (packing the two into FP32 pair instructions measured
+    // slower: the operand pairs had to be assembled from separate words)
 #pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-            const int dir = 2 * A + sg;
-            T* const base = sg == 0 ? sp : sm;
-            if (MODE == 1) {
-                T t = tin[sg * S::ITEMS + S::eoff(A) + local];
+    for (int sg = 0; sg < 2; ++sg) {
+        const int dir = 2 * A + sg;
+        T* const base = sg == 0 ? sp : sm;
+        if (MODE == 1) {
+            T t = tin[sg * S::ITEMS + S::eoff(A) + local];
 #pragma unroll
-                for (int cc = 0; cc < BA; ++cc) {
-                    T* const p = base + (sg == 0 ? cc : BA - 1 - cc) * CST;
-                    T u[NP], dlt[NP];
+            for (int cc = 0; cc < BA; ++cc) {
+                T* const p = base + (sg == 0 ? cc : BA - 1 - cc) * CST;
+                T u[NP], dlt[NP];
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) u[j] = p[j * NS];
+                for (int j = 0; j < NP; ++j) u[j] = p[j * NS];
 #pragma unroll
-                    for (int i = 0; i < NP; ++i) {
-                        T acc = cget<true>(I, csm, dir, i * NP) * u[0];
+                for (int i = 0; i < NP; ++i) {
+                    T acc = cget<BATCH>(I, csm, dir, i * NP) * u[0];
 #pragma unroll
-                        for (int j = 1; j < NP; ++j) acc = fma(cget<true>(I, csm, dir, i * NP + j), u[j], acc);
-                        dlt[i] = fma(cget<true>(I, csm, dir, kOffG + i), t, acc);
-                    }
-                    t = sg == 0 ? u[NP - 1] + dlt[NP - 1] : u[0] + dlt[0];
-#pragma unroll
-                    for (int i = 0; i < NP; ++i) p[i * NS] = fma(T(2), dlt[i], u[i]);
+                    for (int j = 1; j < NP; ++j) acc = fma(cget<BATCH>(I, csm, dir, i * NP + j), u[j], acc);
+                    dlt[i] = fma(cget<BATCH>(I, csm, dir, kOffG + i), t, acc);
                 }
-            } else {
-                const T rho = cget<true>(I, csm, dir, kOffRho);
-                T t = 0;
+                t = sg == 0 ? u[NP - 1] + dlt[NP - 1] : u[0] + dlt[0];
 #pragma unroll
-                for (int cc = 0; cc < BA; ++cc) {
-                    const T* const p = base + (sg == 0 ? cc : BA - 1 - cc) * CST;
-                    T acc = cget<true>(I, csm, dir, kOffProw) * p[0];
-#pragma unroll
-                    for (int j = 1; j < NP; ++j) acc = fma(cget<true>(I, csm, dir, kOffProw + j), p[j * NS], acc);
-                    t = fma(rho, t, acc);
-                }
-                const T last = sg == 0 ? sp[(BA - 1) * CST + (NP - 1) * NS] : sm[0];
-                const int nbk = I.nblk[A], nbs = I.nb[A];
-                const int q = sg == 0 ? bidx : nbk - 1 - bidx;
-                const int Sd = (int)fdiv((unsigned)q, I.fd_nb[A]);
-                const long long gl = I.ax[A].glines;
-                const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
-                const int pop = popP + sg * M;
-                static_cast<T*>(I.sig_out)[(long long)pop * I.sig_stride + (long long)q * gl + gline] = t;
-                if (q - Sd * nbs == nbs - 1)
-                    static_cast<T*>(I.raw_out)[(long long)pop * I.raw_stride + (long long)Sd * gl + gline] = last;
+                for (int i = 0; i < NP; ++i) p[i * NS] = fma(T(2), dlt[i], u[i]);
             }
-        }
-        return;
-    }
-    if (MODE == 1) {
-        T2 Pm[NP][NP], g[NP];
+        } else {
+            const T rho = cget<BATCH>(I, csm, dir, kOffRho);
+            T t = 0;
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            g[i] = pmk(cget<BATCH>(I, csm, 2 * A, kOffG + i), cget<BATCH>(I, csm, 2 * A + 1, kOffG + i));
+            for (int cc = 0; cc < BA; ++cc) {
+                const T* const p = base + (sg == 0 ? cc : BA - 1 - cc) * CST;
+                T acc = cget<BATCH>(I, csm, dir, kOffProw) * p[0];
 #pragma unroll
-            for (int j = 0; j < NP; ++j)
-                Pm[i][j] = pmk(cget<BATCH>(I, csm, 2 * A, i * NP + j), cget<BATCH>(I, csm, 2 * A + 1, i * NP + j));
-        }
-        T2 t = pmk(tin[S::eoff(A) + local], tin[S::ITEMS + S::eoff(A) + local]);
-        const T2 two = pmk(T(2), T(2));
-#pragma unroll
-        for (int cc = 0; cc < BA; ++cc) {
-            T* const p = sp + cc * CST;
-            T* const m = sm + (BA - 1 - cc) * CST;
-            T2 u[NP], dlt[NP];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) u[j] = pmk(p[j * NS], m[j * NS]);
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                T2 acc = pmul(Pm[i][0], u[0]);
-#pragma unroll
-                for (int j = 1; j < NP; ++j) acc = pfma(Pm[i][j], u[j], acc);
-                dlt[i] = pfma(g[i], t, acc);        // f* - f^n at node i
+                for (int j = 1; j < NP; ++j) acc = fma(cget<BATCH>(I, csm, dir, kOffProw + j), p[j * NS], acc);
+                t = fma(rho, t, acc);
             }
-            // outflow traces: node p of the + line, node 0 of the - line
-            t = pmk(u[NP - 1].x + dlt[NP - 1].x, u[0].y + dlt[0].y);
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                const T2 nw = pfma(two, dlt[i], u[i]);
-                p[i * NS] = nw.x;
-                m[i * NS] = nw.y;
-            }
-        }
-    } else {
-        T2 prow[NP];
-#pragma unroll
-        for (int j = 0; j < NP; ++j)
-            prow[j] = pmk(cget<BATCH>(I, csm, 2 * A, kOffProw + j), cget<BATCH>(I, csm, 2 * A + 1, kOffProw + j));
-        const T2 rho = pmk(cget<BATCH>(I, csm, 2 * A, kOffRho), cget<BATCH>(I, csm, 2 * A + 1, kOffRho));
-        T2 t = pmk(T(0), T(0));
-#pragma unroll
-        for (int cc = 0; cc < BA; ++cc) {
-            const T* const p = sp + cc * CST;
-            const T* const m = sm + (BA - 1 - cc) * CST;
-            T2 u[NP];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) u[j] = pmk(p[j * NS], m[j * NS]);
-            T2 acc = pmul(prow[0], u[0]);
-#pragma unroll
-            for (int j = 1; j < NP; ++j) acc = pfma(prow[j], u[j], acc);
-            t = pfma(rho, t, acc);
-        }
-        // the outflow-node values of f (the last cell of each direction)
-        const T lastP = sp[(BA - 1) * CST + (NP - 1) * NS];
-        const T lastM = sm[0];
-        const int nbk = I.nblk[A], nbs = I.nb[A];
-        const long long gl = I.ax[A].glines;
-        const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
-        T* __restrict__ sig = static_cast<T*>(I.sig_out);
-        T* __restrict__ raw = static_cast<T*>(I.raw_out);
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
+            const T last = sg == 0 ? sp[(BA - 1) * CST + (NP - 1) * NS] : sm[0];
+            const int nbk = I.nblk[A], nbs = I.nb[A];
             const int q = sg == 0 ? bidx : nbk - 1 - bidx;
             const int Sd = (int)fdiv((unsigned)q, I.fd_nb[A]);
+            const long long gl = I.ax[A].glines;
+            const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
             const int pop = popP + sg * M;
-            sig[(long long)pop * I.sig_stride + (long long)q * gl + gline] = sg == 0 ? t.x : t.y;
-            if (q - Sd * nbs == nbs - 1)     // downwind-most block of its subdomain
-                raw[(long long)pop * I.raw_stride + (long long)Sd * gl + gline] = sg == 0 ? lastP : lastM;
+            static_cast<T*>(I.sig_out)[(long long)pop * I.sig_stride + (long long)q * gl + gline] = t;
+            if (q - Sd * nbs == nbs - 1)
+                static_cast<T*>(I.raw_out)[(long long)pop * I.raw_stride + (long long)Sd * gl + gline] = last;
         }
     }
 }
