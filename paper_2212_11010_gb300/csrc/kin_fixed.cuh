@@ -122,8 +122,21 @@ struct Shape {
         return want_rp ? best_rp : best_pp;
     }
 
-    static constexpr int RP = best_pad(true);
-    static constexpr int PP = best_pad(false);
+    // Degree 3 in 2D (FP32): a cell row of nodes is one 16-byte word, and
+    // lines are swept four at a time with 16-byte shared-memory accesses
+    // (pm_group4).  Row pad 4 makes the word index of consecutive cell rows
+    // odd apart, and the slab pad makes consecutive populations one word
+    // apart modulo 8, so the 8 words of a quarter warp hit distinct bank
+    // groups for both axes.
+    static constexpr bool G4 = D == 2 && NP == 4 && sizeof(T) == 4 && B1 % 8 == 0 && B0 % 2 == 0 && M == 4;
+    static constexpr int g4_pp()
+    {
+        for (int pp = 0; pp < 32; pp += 4)
+            if (((NROWS * (ROWLEN + 4) + pp) / 4) % 8 == 1) return pp;
+        return 0;
+    }
+    static constexpr int RP = G4 ? 4 : best_pad(true);
+    static constexpr int PP = G4 ? g4_pp() : best_pad(false);
     static constexpr int RSTR = rstr(RP);
     static constexpr int PSTR = pstr(RP, PP);
     static constexpr int TILE = NPOP * PSTR;                        // elements per tile buffer
@@ -249,11 +262,162 @@ __device__ __forceinline__ void pm_item(const Inst& I, int local, int org0, int 
 // Every line item of the tile, axis after axis, spread over all threads
 // (items it, it + NTH, ...).  Axis boundaries fall on warp boundaries for
 // the compiled shapes, so the axis branch does not split a warp.
+// Sweep (MODE 1) or block summaries (MODE 2) of a group of four lines for
+// degree 3 in 2D (Shape::G4).  Group items: first the x groups
+// ((sign, variable) major, y-cell row c1 fastest: the four lines of one row
+// of cells, y-nodes j1 = 0..3), then the y groups ((sign, x-cell) major,
+// variable fastest: the four lines of one column of cells, x-nodes
+// j0 = 0..3).  Every shared-memory access moves one 16-byte word: the four
+// x-nodes of one line of a cell (x groups), or one y-node of all four lines
+// (y groups).  Inflows and summaries of the four lines are consecutive.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int MODE, bool BATCH>
+__device__ __forceinline__ void pm_group4(const Inst& I, int git, int org0, int org1, int bx, int by, T* s,
+                                          const T* tin, const T* csm)
+{
+    using S = Shape<D, P, SYS, T, B0, B1, B2>;
+    constexpr int M = S::M, NN = 16;
+    constexpr int GX = 2 * M * B1;
+    const bool xa = git < GX;
+    int sg, v, c, A;
+    if (xa) {
+        A = 0;
+        sg = git / (M * B1);
+        v = (git / B1) % M;
+        c = git % B1;                   // y-cell row
+    } else {
+        const int gy = git - GX;
+        A = 1;
+        v = gy % M;
+        c = (gy / M) % B0;              // x-cell column
+        sg = gy / (M * B0);
+    }
+    const int dir = 2 * A + sg;
+    const int pop = dir * M + v;
+    T* const slab = s + pop * S::PSTR;
+    const int lineoff = v * S::lines(A) + c * 4;            // item index of line 0 of the group
+    float4* const tin4 = (float4*)(tin + sg * S::ITEMS + S::eoff(A) + lineoff);
+    const int BA = xa ? B0 : B1;
+    auto word = [&](int cc, int j) -> float4* {
+        // cell cc along the sweep axis (already in sweep order), word j
+        const int cell = sg == 0 ? cc : BA - 1 - cc;
+        const int off = xa ? c * S::RSTR + cell * NN : cell * S::RSTR + c * NN;
+        return reinterpret_cast<float4*>(slab + off + 4 * j);
+    };
+    if (MODE == 1) {
+        float Pm[4][4], g[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            g[i] = cget<BATCH>(I, csm, dir, kOffG + i);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Pm[i][j] = cget<BATCH>(I, csm, dir, i * 4 + j);
+        }
+        const float4 t0 = *tin4;
+        float t[4] = {t0.x, t0.y, t0.z, t0.w};
+        // the cell loop is unrolled per axis so that every offset is an immediate
+        auto cellstep = [&](int cc) {
+            float u[4][4];              // u[line][node along the line]
+            float4 w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = *word(cc, j);
+#pragma unroll
+            for (int l = 0; l < 4; ++l)
+#pragma unroll
+                for (int n = 0; n < 4; ++n) {
+                    // x groups: word l holds the nodes of line l; y groups: word n holds node n of all lines
+                    const float4 q = xa ? w[l] : w[n];
+                    const int e = xa ? n : l;
+                    u[l][n] = e == 0 ? q.x : (e == 1 ? q.y : (e == 2 ? q.z : q.w));
+                }
+            float nw[4][4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                float dlt[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float acc = Pm[i][0] * u[l][0];
+#pragma unroll
+                    for (int j = 1; j < 4; ++j) acc = fmaf(Pm[i][j], u[l][j], acc);
+                    dlt[i] = fmaf(g[i], t[l], acc);
+                }
+                t[l] = sg == 0 ? u[l][3] + dlt[3] : u[l][0] + dlt[0];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) nw[l][i] = fmaf(2.0f, dlt[i], u[l][i]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                *word(cc, j) = xa ? make_float4(nw[j][0], nw[j][1], nw[j][2], nw[j][3])
+                                  : make_float4(nw[0][j], nw[1][j], nw[2][j], nw[3][j]);
+        };
+        if (xa) {
+#pragma unroll
+            for (int cc = 0; cc < B0; ++cc) cellstep(cc);
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < B1; ++cc) cellstep(cc);
+        }
+    } else {
+        float prow[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) prow[j] = cget<BATCH>(I, csm, dir, kOffProw + j);
+        const float rho = cget<BATCH>(I, csm, dir, kOffRho);
+        float t[4] = {0.f, 0.f, 0.f, 0.f}, last[4];
+        auto cellsum = [&](int cc, bool final_cell) {
+            float4 w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w[j] = *word(cc, j);
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                float u[4];
+#pragma unroll
+                for (int n = 0; n < 4; ++n) {
+                    const float4 q = xa ? w[l] : w[n];
+                    const int e = xa ? n : l;
+                    u[n] = e == 0 ? q.x : (e == 1 ? q.y : (e == 2 ? q.z : q.w));
+                }
+                float acc = prow[0] * u[0];
+#pragma unroll
+                for (int j = 1; j < 4; ++j) acc = fmaf(prow[j], u[j], acc);
+                t[l] = fmaf(rho, t[l], acc);
+                if (final_cell) last[l] = sg == 0 ? u[3] : u[0];
+            }
+        };
+        if (xa) {
+#pragma unroll
+            for (int cc = 0; cc < B0; ++cc) cellsum(cc, cc == B0 - 1);
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < B1; ++cc) cellsum(cc, cc == B1 - 1);
+        }
+        const int nbk = I.nblk[A], nbs = I.nb[A];
+        const int bidx = xa ? bx : by;
+        const int q = sg == 0 ? bidx : nbk - 1 - bidx;
+        const int Sd = (int)fdiv((unsigned)q, I.fd_nb[A]);
+        const long long gl = I.ax[A].glines;
+        // lines (cell c of the transverse axis, node 0..3): glines 4 (origin + c) + 0..3
+        const long long gline0 = 4LL * ((xa ? org1 : org0) + c);
+        *reinterpret_cast<float4*>(static_cast<float*>(I.sig_out) + (long long)pop * I.sig_stride +
+                                   (long long)q * gl + gline0) = make_float4(t[0], t[1], t[2], t[3]);
+        if (q - Sd * nbs == nbs - 1)
+            *reinterpret_cast<float4*>(static_cast<float*>(I.raw_out) + (long long)pop * I.raw_stride +
+                                       (long long)Sd * gl + gline0) = make_float4(last[0], last[1], last[2], last[3]);
+    }
+}
+
 template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH, int MODE, bool BATCH>
 __device__ __forceinline__ void fixed_pm_all(const Inst& I, int org0, int org1, int org2, int bx, int by, int bz,
                                              T* s, const T* tin, const T* csm)
 {
     using S = Shape<D, P, SYS, T, B0, B1, B2>;
+    if constexpr (S::G4) {
+        constexpr int NG = 2 * S::M * (B0 + B1);
+#pragma unroll
+        for (int k = 0; k < (NG + NTH - 1) / NTH; ++k) {
+            const int git = threadIdx.x + k * NTH;
+            if (NG % NTH != 0 && git >= NG) break;
+            pm_group4<D, P, SYS, T, B0, B1, B2, MODE, BATCH>(I, git, org0, org1, bx, by, s, tin, csm);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < (S::ITEMS + NTH - 1) / NTH; ++k) {
         const int it = threadIdx.x + k * NTH;
