@@ -234,6 +234,12 @@ kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int de
  * KIN_ECUDA, KIN_ENOMEM; messages from kin_batch_last_error. */
 typedef struct kin_batch kin_batch;
 kin_status kin_batch_create(kin_ctx* const* members, int count, void* stream, kin_batch** out);
+/* As kin_batch_create, with flags: KIN_BATCH_DIRECT enqueues each step's
+ * launches directly instead of capturing and replaying CUDA graphs (cheaper
+ * to create: for batches whose membership changes often, as in a serving
+ * loop).  Results are the same.  Unknown flags: KIN_EINVAL. */
+enum { KIN_BATCH_DIRECT = 1 };
+kin_status kin_batch_create_ex(kin_ctx* const* members, int count, void* stream, int flags, kin_batch** out);
 kin_status kin_batch_step(kin_batch* batch, int nsteps);
 kin_status kin_batch_sync(kin_batch* batch);
 kin_status kin_batch_destroy(kin_batch* batch);

@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
 
 EXPORTED = ["kin_create", "kin_set_state", "kin_set_kinetic", "kin_step", "kin_get_state",
             "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error",
-            "kin_step_noalloc", "kin_batch_create", "kin_batch_step", "kin_batch_sync",
+            "kin_step_noalloc", "kin_batch_create", "kin_batch_create_ex", "kin_batch_step", "kin_batch_sync",
             "kin_batch_destroy", "kin_batch_last_error"]
 
 
@@ -105,6 +105,7 @@ def load_library():
                                      ctypes.c_double, ctypes.POINTER(kin_opts), vp, ctypes.c_int,
                                      ctypes.c_char_p, sz]
     lib.kin_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.kin_batch_create_ex.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(vp)]
     lib.kin_batch_step.argtypes = [vp, ctypes.c_int]
     lib.kin_batch_sync.argtypes = [vp]
     lib.kin_batch_destroy.argtypes = [vp]
@@ -245,12 +246,24 @@ def _bcheck(batch, status):
         raise KinError(status, load_library().kin_batch_last_error(batch).decode())
 
 
+KIN_BATCH_DIRECT = 1
+
+
 def kin_batch_create(ctxs, stream=None):
     """Batch of contexts stepped together (one launch per kernel type per step)."""
     lib = load_library()
     arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
     out = ctypes.c_void_p()
     _bcheck(None, lib.kin_batch_create(arr, len(ctxs), stream, ctypes.byref(out)))
+    return out
+
+
+def kin_batch_create_ex(ctxs, stream=None, flags=0):
+    """kin_batch_create with flags (KIN_BATCH_DIRECT: no CUDA graphs)."""
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    out = ctypes.c_void_p()
+    _bcheck(None, lib.kin_batch_create_ex(arr, len(ctxs), stream, int(flags), ctypes.byref(out)))
     return out
 
 
@@ -308,9 +321,10 @@ def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 
 class Batch:
     """Owning wrapper of a kin_batch over Context objects (which must outlive it)."""
 
-    def __init__(self, contexts, stream=None):
+    def __init__(self, contexts, stream=None, graphs=True):
         self.contexts = list(contexts)
-        self.handle = kin_batch_create([c.ctx for c in self.contexts], stream)
+        flags = 0 if graphs else KIN_BATCH_DIRECT
+        self.handle = kin_batch_create_ex([c.ctx for c in self.contexts], stream, flags)
 
     def step(self, n=1):
         kin_batch_step(self.handle, n)

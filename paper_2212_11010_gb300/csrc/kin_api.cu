@@ -963,6 +963,7 @@ struct kin_batch {
     std::vector<void*> dev;           // device allocations of the batch
     std::vector<cudaEvent_t> ev_member;
     cudaEvent_t ev_done = nullptr;
+    bool direct = false;              // enqueue the launches per step instead of replaying graphs
     cudaStream_t stream = nullptr;
     bool own_stream = false;          // created here because the caller passed NULL
     cudaGraphExec_t g2[2] = {nullptr, nullptr};   // two steps starting at parity q
@@ -1045,7 +1046,14 @@ static cudaError_t batch_capture(kin_batch* b, int q, int nsteps, cudaGraphExec_
 
 extern "C" kin_status kin_batch_create(kin_ctx* const* members, int count, void* stream, kin_batch** out)
 {
+    return kin_batch_create_ex(members, count, stream, 0, out);
+}
+
+extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, void* stream, int flags,
+                                          kin_batch** out)
+{
     if (!out) return batch_fail(nullptr, KIN_EINVAL, "out is NULL");
+    if (flags & ~KIN_BATCH_DIRECT) return batch_fail(nullptr, KIN_EINVAL, "unknown flags 0x%x", flags);
     *out = nullptr;
     if (!members || count < 1) return batch_fail(nullptr, KIN_EINVAL, "need at least one member");
     for (int i = 0; i < count; ++i) {
@@ -1144,7 +1152,8 @@ extern "C" kin_status kin_batch_create(kin_ctx* const* members, int count, void*
     for (int i = 0; i < count && e == cudaSuccess; ++i)
         e = cudaEventCreateWithFlags(&b->ev_member[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_done, cudaEventDisableTiming);
-    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    b->direct = (flags & KIN_BATCH_DIRECT) != 0;
+    for (int q = 0; q < 2 && e == cudaSuccess && !b->direct; ++q) {
         e = batch_capture(b, q, 2, &b->g2[q]);
         if (e == cudaSuccess) e = batch_capture(b, q, 1, &b->g1[q]);
     }
@@ -1176,14 +1185,21 @@ extern "C" kin_status kin_batch_step(kin_batch* b, int nsteps)
         e = cudaEventRecord(b->ev_member[i], b->members[i]->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_member[i], 0);
     }
-    int left = nsteps;
-    while (e == cudaSuccess && left >= 2) {
-        e = cudaGraphLaunch(b->g2[b->parity], b->stream);
-        left -= 2;
-    }
-    if (e == cudaSuccess && left == 1) {
-        e = cudaGraphLaunch(b->g1[b->parity], b->stream);
-        b->parity ^= 1;
+    if (b->direct) {
+        for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
+            e = batch_enqueue_step(b, b->parity);
+            b->parity ^= 1;
+        }
+    } else {
+        int left = nsteps;
+        while (e == cudaSuccess && left >= 2) {
+            e = cudaGraphLaunch(b->g2[b->parity], b->stream);
+            left -= 2;
+        }
+        if (e == cudaSuccess && left == 1) {
+            e = cudaGraphLaunch(b->g1[b->parity], b->stream);
+            b->parity ^= 1;
+        }
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_done, b->stream);
     for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i)

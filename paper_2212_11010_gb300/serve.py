@@ -51,21 +51,28 @@ class Server:
 
     def run(self, requests, workload_of, clock=time.perf_counter):
         """requests: objects with rid, arrival (s), steps; workload_of(r) -> Workload.
-        Returns the Served records in request order."""
+        Returns the Served records in request order.
+
+        Each round enqueues one chunk of steps for the active batch, admits
+        the requests that have arrived meanwhile (context creation and
+        initial state run on the new contexts' own streams while the chunk
+        runs), then waits for the chunk, retires finished requests and folds
+        the admitted ones into the next batch."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         records = {r.rid: Served(r.rid, r.arrival) for r in requests}
-        active = []            # (record, context, remaining steps, bytes)
+        active = []            # [record, context, remaining steps, bytes]
         used = 0.0
         batch = None
-        dirty = False
         t0 = clock()
-        while pending or active:
-            now = clock() - t0
+
+        def admit(now):
+            nonlocal used
+            new = []
             while pending and pending[0].arrival <= now:
                 r = pending[0]
                 w = workload_of(r)
                 need = state_bytes_estimate(w)
-                if used + need > self.budget and active:
+                if used + need > self.budget and (active or new):
                     break                                  # wait for memory to free up
                 pending.popleft()
                 ctx = Context.from_workload(w, precision=KIN_FP32, torch_alloc=self.torch_alloc)
@@ -75,40 +82,46 @@ class Server:
                 rec.steps = r.steps
                 rec.dofs = w.kinetic_dofs
                 used += ctx.info.device_bytes
-                active.append([rec, ctx, r.steps, ctx.info.device_bytes])
-                dirty = True
-            if not active:
+                new.append([rec, ctx, r.steps, ctx.info.device_bytes])
+            return new
+
+        while pending or active:
+            k = 0
+            if active:
+                if batch is None:
+                    # membership changes every few chunks: direct launches, no graph capture
+                    batch = Batch([a[1] for a in active], graphs=False)
+                k = min(self.chunk, min(a[2] for a in active))
+                batch.step(k)                              # asynchronous
+            new = admit(clock() - t0)                      # overlaps the chunk
+            if not active and not new:
                 if pending:
                     time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
                 continue
-            if dirty:
-                if batch is not None:
-                    batch.close()
-                batch = Batch([a[1] for a in active])
-                dirty = False
-            k = min(self.chunk, min(a[2] for a in active))
-            batch.step(k)
-            batch.sync()
             still = []
-            for a in active:
-                a[2] -= k
-                if a[2] == 0:
-                    rec, ctx = a[0], a[1]
-                    W = ctx.get_state()
-                    rec.finished = clock() - t0
-                    if self.keep_results:
-                        rec.result = W
-                    used -= a[3]
-                    dirty = True
-                else:
-                    still.append(a)
-            if dirty and batch is not None:
+            if active:
+                batch.sync()
+                for a in active:
+                    a[2] -= k
+                    if a[2] == 0:
+                        rec, ctx = a[0], a[1]
+                        W = ctx.get_state()
+                        rec.finished = clock() - t0
+                        if self.keep_results:
+                            rec.result = W
+                        used -= a[3]
+                    else:
+                        still.append(a)
+                if len(still) != len(active) or new:
+                    batch.close()
+                    batch = None
+                for a in active:
+                    if a[2] == 0:
+                        a[1].close()
+            elif new and batch is not None:
                 batch.close()
                 batch = None
-            for a in active:
-                if a[2] == 0:
-                    a[1].close()
-            active = still
+            active = still + new
         if batch is not None:
             batch.close()
         return [records[r.rid] for r in requests]

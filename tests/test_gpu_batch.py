@@ -63,6 +63,23 @@ def test_batch_equals_members_alone(kin):
         c.close()
 
 
+def test_direct_batch_equals_graph_batch(kin):
+    """Direct launches per step (no CUDA graphs) give the graph-replay result."""
+    ws, blocks = _mix()
+    res = []
+    for graphs in (True, False):
+        ctxs = [_ctx(kin, w, b) for w, b in zip(ws, blocks)]
+        with kin.Batch(ctxs, graphs=graphs) as batch:
+            batch.step(3)
+            batch.step(2)
+            batch.sync()
+        res.append([c.get_kinetic() for c in ctxs])
+        for c in ctxs:
+            c.close()
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
 def test_batch_members_with_different_parity_and_oracle(kin):
     ws, blocks = _mix()
     ws, blocks = ws[:3], blocks[:3]
