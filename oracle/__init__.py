@@ -26,6 +26,7 @@ _LIB = os.path.join(_HERE, "libkin_oracle.so")
 
 ADVECTION = 0
 EULER = 1
+MAXWELL = 2     # 3D, W = (E, H)
 AXIS = 0        # 2d velocities +-lambda e_a (D1Q2, D2Q4, D3Q6)
 SIMPLEX = 1     # d + 1 velocities (D1Q2, D2Q3, D3Q4)
 
@@ -64,6 +65,7 @@ class _Problem(ctypes.Structure):
         ("tiles", ctypes.c_int * 3),
         ("iters", ctypes.c_int),
         ("velset", ctypes.c_int),
+        ("sigma", ctypes.c_double),
     ]
 
 
@@ -129,6 +131,7 @@ class Problem:
     tiles: tuple = (1, 1, 1)
     iters: int = 3
     velset: int = AXIS
+    sigma: float = 0.0
     _c: _Problem = field(default=None, repr=False, compare=False)
 
     def c(self) -> _Problem:
@@ -150,6 +153,7 @@ class Problem:
         p.tiles = (ctypes.c_int * 3)(*pad(self.tiles, 1))
         p.iters = self.iters
         p.velset = self.velset
+        p.sigma = self.sigma
         self._c = p
         return p
 

@@ -58,7 +58,8 @@ static int check_problem(const ko_problem* P)
     if (!P) return -1;
     if (P->dim < 1 || P->dim > 3) return -2;
     if (P->degree < 1 || P->degree > KO_MAXP) return -3;
-    if (P->system != KO_ADVECTION && P->system != KO_EULER) return -4;
+    if (P->system != KO_ADVECTION && P->system != KO_EULER && P->system != KO_MAXWELL) return -4;
+    if (P->system == KO_MAXWELL && (P->dim != 3 || !(P->sigma >= 0.0))) return -4;
     for (int a = 0; a < 3; ++a) {
         if (a < P->dim) {
             if (P->n[a] < 1 || P->tiles[a] < 1 || P->n[a] % P->tiles[a]) return -5;
@@ -73,7 +74,11 @@ static int check_problem(const ko_problem* P)
     return 0;
 }
 
-int ko_num_vars(const ko_problem* P) { return P->system == KO_EULER ? P->dim + 2 : 1; }
+int ko_num_vars(const ko_problem* P)
+{
+    if (P->system == KO_MAXWELL) return 6;
+    return P->system == KO_EULER ? P->dim + 2 : 1;
+}
 int ko_num_vel(const ko_problem* P)
 {
     return (P->velset == KO_SIMPLEX && P->dim > 1) ? P->dim + 1 : 2 * P->dim;
@@ -214,6 +219,25 @@ int ko_flux(const ko_problem* P, const double* W, int axis, double* Q)
     if (axis < 0 || axis >= P->dim) return -1;
     if (P->system == KO_ADVECTION) {
         Q[0] = P->adv[axis] * W[0];
+        return 0;
+    }
+    if (P->system == KO_MAXWELL) {
+        /* Sec. 6.1.1: Q(W, N) = (-N x H, N x E) with N = e_axis; the cross
+         * product N x v written component by component */
+        const double* E = W;
+        const double* H = W + 3;
+        double NxE[3] = {0, 0, 0}, NxH[3] = {0, 0, 0};
+        const int i = axis, j = (axis + 1) % 3, k = (axis + 2) % 3;
+        /* e_i x v = e_i x (v_j e_j + v_k e_k) = v_j e_k - v_k e_j */
+        NxE[k] = E[j];
+        NxE[j] = -E[k];
+        NxH[k] = H[j];
+        NxH[j] = -H[k];
+        (void)i;
+        for (int c = 0; c < 3; ++c) {
+            Q[c] = -NxH[c];
+            Q[3 + c] = NxE[c];
+        }
         return 0;
     }
     int d = P->dim;
@@ -655,6 +679,19 @@ int ko_relax(const ko_problem* P, double* f)
             W[v] = s;
         }
         ko_maxwellian(P, W, M);
+        if (P->system == KO_MAXWELL) {
+            /* source step on W (Crank-Nicolson in time), then relaxation of
+             * the non-equilibrium part about the equilibrium of the new W */
+            const double mu = (1.0 - 0.5 * P->sigma * P->dt) / (1.0 + 0.5 * P->sigma * P->dt);
+            double Wp[8], Mp[64];
+            for (int v = 0; v < m; ++v) Wp[v] = v < 3 ? mu * W[v] : W[v];
+            ko_maxwellian(P, Wp, Mp);
+            for (int pop = 0; pop < nv * m; ++pop) {
+                double* fp = f + (size_t)pop * nodes + i;
+                *fp = Mp[pop] + (1.0 - P->omega) * (*fp - M[pop]);
+            }
+            continue;
+        }
         for (int pop = 0; pop < nv * m; ++pop) {
             double* fp = f + (size_t)pop * nodes + i;
             *fp = P->omega * M[pop] + (1.0 - P->omega) * (*fp);

@@ -9,7 +9,9 @@
  * header, table or helper with the GPU library.
  *
  * Conventions (identical on both sides, but written separately):
- *   d        space dimension (1..3), m conserved variables.
+ *   d        space dimension (1..3), m conserved variables.  Systems:
+ *            scalar advection (m = 1), Euler (m = d + 2) and, in 3D,
+ *            Maxwell's equations (Sec. 6.1.1; m = 6, W = (E, H)).
  *   k        kinetic velocity index.  Axis sets (velset KO_AXIS; D1Q2, D2Q4,
  *            D3Q6): k = 2*a + s, V_k = +lambda e_a (s = 0) or -lambda e_a
  *            (s = 1).  Simplex sets (velset KO_SIMPLEX; d + 1 velocities,
@@ -32,7 +34,7 @@
 extern "C" {
 #endif
 
-enum { KO_ADVECTION = 0, KO_EULER = 1 };
+enum { KO_ADVECTION = 0, KO_EULER = 1, KO_MAXWELL = 2 };
 enum { KO_AXIS = 0, KO_SIMPLEX = 1 };
 
 typedef struct {
@@ -50,6 +52,7 @@ typedef struct {
     int tiles[3];       /* subdomains per axis; must divide n[a]              */
     int iters;          /* subdomain iterations K (>= 1); 0 = to fixed point  */
     int velset;         /* KO_AXIS (2d velocities) or KO_SIMPLEX (d + 1)      */
+    double sigma;       /* conductivity (Maxwell only; uniform), >= 0         */
 } ko_problem;
 
 int    ko_num_vars(const ko_problem* P);          /* m                      */
@@ -86,7 +89,11 @@ int ko_moments(const ko_problem* P, const double* f, double* W);
  * that the finite iteration count leaves at subdomain interfaces.
  * If iters_done != NULL it receives the number of iterations used. */
 int ko_transport(const ko_problem* P, double* f, double* defect, int* iters_done);
-/* Over-relaxation f <- omega M(W) + (1 - omega) f (eq. over_relaxation). */
+/* Over-relaxation f <- omega M(W) + (1 - omega) f (eq. over_relaxation).
+ * Maxwell with conductivity sigma: first the Crank-Nicolson source step of
+ * Sec. 2.3 on W = sum f (E <- mu E, H unchanged, mu = (1 - sigma dt/2) /
+ * (1 + sigma dt/2), Sec. 6.4), then the non-equilibrium part relaxed about
+ * the new equilibrium: f <- M(W+) + (1 - omega)(f - M(W-)). */
 int ko_relax(const ko_problem* P, double* f);
 /* nsteps applications of S(dt) = relaxation o transport. */
 int ko_step(const ko_problem* P, double* f, int nsteps);

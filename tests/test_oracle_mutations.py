@@ -44,10 +44,17 @@ MUTATIONS = {
                            "{{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, -1}}"),
     "moment_row_velocity_component": ("for (int a = 0; a < d; ++a) A[(1 + a) * nv + k] = V[a];",
                                       "for (int a = 0; a < d; ++a) A[(1 + a) * nv + k] = V[d - 1 - a];"),
+    "maxwell_cross_product_sign": ("NxE[k] = E[j];", "NxE[k] = -E[j];"),
+    "maxwell_source_factor_inverted": ("const double mu = (1.0 - 0.5 * P->sigma * P->dt) / (1.0 + 0.5 * P->sigma * P->dt);",
+                                       "const double mu = (1.0 + 0.5 * P->sigma * P->dt) / (1.0 - 0.5 * P->sigma * P->dt);"),
+    "maxwell_source_damps_h": ("Wp[v] = v < 3 ? mu * W[v] : W[v];", "Wp[v] = mu * W[v];"),
+    "maxwell_literal_relaxation": ("*fp = Mp[pop] + (1.0 - P->omega) * (*fp - M[pop]);",
+                                   "*fp = P->omega * Mp[pop] + (1.0 - P->omega) * (*fp);"),
 }
 
 PIN_FILES = ["tests/test_oracle_basis.py", "tests/test_oracle_relaxation.py",
-             "tests/test_oracle_transport.py", "tests/test_oracle_simplex.py"]
+             "tests/test_oracle_transport.py", "tests/test_oracle_simplex.py",
+             "tests/test_oracle_maxwell.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
