@@ -42,19 +42,23 @@ ALGO_BYTES_PER_DOF = {"f32": 8, "f64": 16}   # read f^n once + write f^{n+1} onc
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
 
-def flops_per_dof(dim, degree, m, nvel):
+def flops_per_dof(dim, degree, m, nvel, maxwell=False):
     """FP64 floating-point operations of one step per kinetic DOF, counted from
     the axis-velocity scheme as the kernels evaluate it (an FMA is 2 flop):
     sweep per cell line of NP nodes: NP rows of (P - I) u (2 NP) plus g t (2),
     the outflow trace (1) and f^{n+1} = u + 2 delta (2 per node); block
     summary per cell line: outflow row (2 NP) and gain (2); relaxation per
     node: the moment sums, Euler pressure and fluxes, and two Maxwellian
-    updates per (axis, variable); the look-back is below 1 flop per DOF."""
+    updates per (axis, variable); for Maxwell the conductivity factor on E and
+    both Maxwellians (before and after it) per (axis, variable); the
+    look-back is below 1 flop per DOF."""
     NP = degree + 1
     sweep = (NP * (2 * NP + 2) + 1 + 2 * NP) / NP
     summary = (2 * NP + 2) / NP
     npop = nvel * m
-    if m == 1:
+    if maxwell:
+        relax = m * (nvel - 1) + 3 + dim * m * 14
+    elif m == 1:
         relax = (nvel - 1) + dim * (1 + 2 + 2 * 4)
     else:
         relax = m * (nvel - 1) + (1 + 2 * dim + 4) + dim * (1 + 2 * dim + 3 + m * 8)
@@ -82,6 +86,9 @@ def make_workload(name):
     elif name == "densitywave3d-d3q4":
         w = workloads.densitywave3d(seed=0, velset=1)
         desc = "densitywave3d-euler-128^3-p1-D3Q4-16^3sub-K3"
+    elif name == "maxwell3d":
+        w = workloads.maxwell3d(seed=0, n=128, degree=1, tiles=16, sigma=1.0)
+        desc = "maxwell3d-128^3-p1-D3Q6-16^3sub-K3-sigma1"
     else:
         raise SystemExit(f"unknown workload {name}")
     return w, desc
@@ -341,7 +348,7 @@ def run_ours(args):
     algo_bytes = ALGO_BYTES_PER_DOF[prec] * dofs
     achieved = algo_bytes / (ms_per_step * 1e-3) / 1e9
     if prec == "f64" and w.velset == 0:
-        fpd = flops_per_dof(w.dim, w.degree, w.m, 2 * w.dim)
+        fpd = flops_per_dof(w.dim, w.degree, w.m, 2 * w.dim, maxwell=w.system == 2)  # Maxwell system id
         tflops = fpd * dofs / (ms_per_step * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None, "peak_kind": "derived-fp64-units",
@@ -525,7 +532,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="vortex2d",
                     choices=["vortex2d", "densitywave3d", "advection1d", "batched", "serving",
-                             "vortex2d-d2q3", "densitywave3d-d3q4"])
+                             "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d"])
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

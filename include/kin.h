@@ -56,7 +56,10 @@ typedef enum {
     KIN_ESTATE = 6      /* context poisoned by an earlier error, or no state  */
 } kin_status;
 
-enum { KIN_ADVECTION = 0, KIN_EULER = 1 };          /* kin_model.system   */
+/* kin_model.system: scalar advection (m = 1), Euler (m = d + 2), or
+ * Maxwell's equations in 3D (Sec. 6.1.1; m = 6, W = (E, H), axis velocity
+ * set D3Q6 only) with a uniform conductivity kin_model.sigma. */
+enum { KIN_ADVECTION = 0, KIN_EULER = 1, KIN_MAXWELL = 2 };
 /* kin_model.velset: 2d axis velocities +-lambda e_a (D1Q2, D2Q4, D3Q6; the
  * value is the dimension), or the paper's d + 1 sets: D2Q3 with
  * V_k = lambda (cos 2k pi/3, sin 2k pi/3) (Sec. 2.4) and D3Q4 with the cube
@@ -80,7 +83,13 @@ typedef struct {
 /* Kinetic model.  lambda: kinetic speed |V_k| (must satisfy the
  * sub-characteristic condition of Sec. 2.1 for the data; the library does not
  * check it).  omega in [1, 2] (eq. over_relaxation).  gamma: Euler gas
- * constant.  adv: advection velocity of the scalar law. */
+ * constant.  adv: advection velocity of the scalar law.  sigma: Maxwell
+ * conductivity (>= 0, uniform; ignored by the other systems): each step
+ * applies the Crank-Nicolson source step of Sec. 2.3 to W = sum f,
+ * E <- mu E with mu = (1 - sigma dt/2) / (1 + sigma dt/2) (Sec. 6.4), and
+ * relaxes the non-equilibrium part about the new equilibrium,
+ * f <- M(W+) + (1 - omega)(f - M(W-)) (for sigma = 0 this is
+ * eq. over_relaxation). */
 typedef struct {
     int system;
     int velset;
@@ -88,6 +97,7 @@ typedef struct {
     double gamma;
     double adv[3];
     double omega;
+    double sigma;
 } kin_model;
 
 /* Device allocator hook: called with the context's stream.  Both NULL means

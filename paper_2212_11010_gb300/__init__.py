@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libkin.so")
 
 KIN_OK, KIN_EINVAL, KIN_ENOMEM, KIN_EBUDGET, KIN_ECUDA, KIN_ETIMEOUT, KIN_ESTATE = range(7)
-KIN_ADVECTION, KIN_EULER = 0, 1
+KIN_ADVECTION, KIN_EULER, KIN_MAXWELL = 0, 1, 2
 KIN_D1Q2, KIN_D2Q4, KIN_D3Q6, KIN_D2Q3, KIN_D3Q4 = 1, 2, 3, 4, 5
 KIN_FP64, KIN_FP32 = 0, 1
 KIN_DEBUG_STALL_LOAD = 1
@@ -49,7 +49,8 @@ class kin_mesh(ctypes.Structure):
 
 class kin_model(ctypes.Structure):
     _fields_ = [("system", ctypes.c_int), ("velset", ctypes.c_int), ("lam", ctypes.c_double),
-                ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 3), ("omega", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("adv", ctypes.c_double * 3), ("omega", ctypes.c_double),
+                ("sigma", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -294,12 +295,12 @@ def kin_last_error(ctx=None) -> str:
 def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 0.0),
               tiles=(1, 1, 1), iters=3, precision=KIN_FP64, block=(0, 0, 0), mem_budget=0,
               stream=None, torch_alloc=False, wait_timeout_s=0.0, debug_flags=0, threads=0, stages=0,
-              velset=None):
+              velset=None, sigma=0.0):
     pad = lambda t, fill: tuple(t) + (fill,) * (3 - len(tuple(t)))
     mesh = kin_mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
                     (ctypes.c_double * 3)(*pad(hi, 1.0)))
     model = kin_model(system, dim if velset is None else velset, lam, gamma,
-                      (ctypes.c_double * 3)(*pad(adv, 0.0)), omega)
+                      (ctypes.c_double * 3)(*pad(adv, 0.0)), omega, sigma)
     opts = kin_opts()
     opts.tiles = (ctypes.c_int * 3)(*pad(tiles, 1))
     opts.iters = iters
@@ -364,7 +365,8 @@ class Context:
         prec = precision if precision is not None else (KIN_FP32 if w.precision == "f32" else KIN_FP64)
         vs = {2: KIN_D2Q3, 3: KIN_D3Q4}.get(w.dim) if getattr(w, "velset", 0) == 1 else None
         return cls(w.dim, w.n, w.lo, w.hi, w.degree, w.system, w.lam, w.dt, omega=w.omega,
-                   gamma=w.gamma, adv=w.adv, tiles=w.tiles, iters=w.iters, precision=prec, velset=vs, **kw)
+                   gamma=w.gamma, adv=w.adv, tiles=w.tiles, iters=w.iters, precision=prec, velset=vs,
+                   sigma=getattr(w, "sigma", 0.0), **kw)
 
     @property
     def dtype(self):

@@ -22,7 +22,7 @@ struct kin_ctx {
     // problem
     int dim = 1, n[3] = {1, 1, 1}, degree = 1, system = 0, m = 1, nvel = 2, npop = 2, NP = 2, NN = 2;
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
-    double lambda = 1, gamma = 1.4, adv[3] = {0, 0, 0}, omega = 2, dt = 0;
+    double lambda = 1, gamma = 1.4, adv[3] = {0, 0, 0}, omega = 2, dt = 0, sigma = 0;
     int tiles[3] = {1, 1, 1}, L[3] = {1, 1, 1}, iters = 3, precision = KIN_FP64;
     int B[3] = {1, 1, 1}, nblk[3] = {1, 1, 1}, nb[3] = {1, 1, 1};
     size_t cells = 0, nodes = 0, sig_stride = 0, raw_stride = 0, esize = 8;
@@ -245,6 +245,7 @@ static Inst make_inst(const kin_ctx* c, int mode)
     I.lambda = c->lambda;
     I.gamma = c->gamma;
     I.omega = c->omega;
+    I.mu = c->system == KIN_MAXWELL ? (1.0 - 0.5 * c->sigma * c->dt) / (1.0 + 0.5 * c->sigma * c->dt) : 1.0;
     return I;
 }
 
@@ -450,8 +451,12 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     if (!mesh || !model || !opts) return fail(nullptr, KIN_EINVAL, "mesh, model and opts are required");
     if (mesh->dim < 1 || mesh->dim > 3) return fail(nullptr, KIN_EINVAL, "dim must be 1..3");
     if (degree < 1 || degree > 3) return fail(nullptr, KIN_EINVAL, "degree must be 1..3");
-    if (model->system != KIN_ADVECTION && model->system != KIN_EULER)
+    if (model->system != KIN_ADVECTION && model->system != KIN_EULER && model->system != KIN_MAXWELL)
         return fail(nullptr, KIN_EINVAL, "unknown system %d", model->system);
+    if (model->system == KIN_MAXWELL && (mesh->dim != 3 || model->velset != KIN_D3Q6))
+        return fail(nullptr, KIN_EINVAL, "Maxwell's equations need dim 3 and the D3Q6 velocity set");
+    if (model->system == KIN_MAXWELL && !(model->sigma >= 0.0))
+        return fail(nullptr, KIN_EINVAL, "the conductivity sigma must be >= 0");
     const bool simplex = (model->velset == KIN_D2Q3 && mesh->dim == 2) ||
                          (model->velset == KIN_D3Q4 && mesh->dim == 3);
     if (model->velset != mesh->dim && !simplex)
@@ -479,7 +484,8 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     c->dim = mesh->dim;
     c->degree = degree;
     c->system = model->system;
-    c->m = model->system == KIN_EULER ? mesh->dim + 2 : 1;
+    c->m = model->system == KIN_MAXWELL ? 6 : (model->system == KIN_EULER ? mesh->dim + 2 : 1);
+    c->sigma = model->sigma;
     c->simplex = simplex;
     c->nvel = simplex ? mesh->dim + 1 : 2 * mesh->dim;
     c->npop = c->nvel * c->m;
@@ -582,7 +588,7 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
         ALLOC(c->c64, sizeof(double) * 6 * kCoefStride);
         ALLOC(c->gll, sizeof(double) * 2 * kMaxNP);
         ALLOC(c->Wbuf, sizeof(double) * c->m * c->nodes);
-        ALLOC(c->partial, sizeof(double) * kDiagBlocks * 6);
+        ALLOC(c->partial, sizeof(double) * kDiagBlocks * (kMaxVars + 1));
         ALLOC(c->result, sizeof(double) * 16);
         ALLOC(c->errword, sizeof(int) * 4);
 #undef ALLOC
@@ -693,7 +699,7 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     ALLOC(c->coef, c->esize == 4 ? sizeof(float) * 6 * kCoefStride : 16);
     ALLOC(c->gll, sizeof(double) * 2 * kMaxNP);
     ALLOC(c->Wbuf, sizeof(double) * c->m * c->nodes);
-    ALLOC(c->partial, sizeof(double) * kDiagBlocks * 6);
+    ALLOC(c->partial, sizeof(double) * kDiagBlocks * (kMaxVars + 1));
     ALLOC(c->result, sizeof(double) * 8);
     ALLOC(c->errword, sizeof(int) * 4);
 #undef ALLOC
@@ -846,7 +852,7 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
     if (mass_per_var) {
         KIN_CUDA(c, launch_mass(point_args(c), c->f, c->gll, c->partial, c->result,
                                 c->precision == KIN_FP32, c->stream));
-        KIN_CUDA(c, cudaMemcpyAsync(host, c->result, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->stream));
+        KIN_CUDA(c, cudaMemcpyAsync(host, c->result, sizeof(double) * kMaxVars, cudaMemcpyDeviceToHost, c->stream));
         KIN_CUDA(c, cudaStreamSynchronize(c->stream));
         for (int v = 0; v < c->m; ++v) mass_per_var[v] = host[v];
     }
@@ -881,11 +887,12 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
         }
         KIN_CUDA(c, launch_defect(da, c->sig[c->cur], c->raw[c->cur], c->c64, c->gll, c->partial,
                                   c->result, c->precision == KIN_FP32, c->stream));
-        KIN_CUDA(c, cudaMemcpyAsync(host, c->result, sizeof(double) * 6, cudaMemcpyDeviceToHost, c->stream));
+        KIN_CUDA(c, cudaMemcpyAsync(host, c->result, sizeof(double) * (kMaxVars + 1), cudaMemcpyDeviceToHost,
+                                    c->stream));
         KIN_CUDA(c, cudaStreamSynchronize(c->stream));
         if (next_defect)
             for (int v = 0; v < c->m; ++v) next_defect[v] = host[v];
-        if (iter_residual) *iter_residual = host[5];
+        if (iter_residual) *iter_residual = host[kMaxVars];
     }
     return check_errword(c);
 }
@@ -1296,7 +1303,8 @@ extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* mo
         return KIN_EINVAL;
     }
     if (mesh->dim < 1 || mesh->dim > 3 || degree < 1 || degree > 3 ||
-        (model->system != KIN_ADVECTION && model->system != KIN_EULER) || model->velset != mesh->dim ||
+        (model->system != KIN_ADVECTION && model->system != KIN_EULER && model->system != KIN_MAXWELL) ||
+        (model->system == KIN_MAXWELL && (mesh->dim != 3 || !(model->sigma >= 0.0))) || model->velset != mesh->dim ||
         !(model->lambda > 0) || !(dt > 0) || !(model->omega >= 1.0 && model->omega <= 2.0) ||
         (model->system == KIN_EULER && !(model->gamma > 1.0)) || opts->iters < 1 ||
         (opts->precision != KIN_FP64 && opts->precision != KIN_FP32)) {
@@ -1310,7 +1318,8 @@ extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* mo
     c.dim = mesh->dim;
     c.degree = degree;
     c.system = model->system;
-    c.m = model->system == KIN_EULER ? mesh->dim + 2 : 1;
+    c.m = model->system == KIN_MAXWELL ? 6 : (model->system == KIN_EULER ? mesh->dim + 2 : 1);
+    c.sigma = model->sigma;
     c.nvel = 2 * mesh->dim;
     c.npop = c.nvel * c.m;
     c.NP = degree + 1;

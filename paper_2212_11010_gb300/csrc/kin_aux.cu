@@ -148,11 +148,22 @@ __global__ void setup_kernel(SetupArgs A)
 // point-wise kernels (grid-stride over nodes)
 // ---------------------------------------------------------------------------
 
-// Euler or advection flux in FP64 (eq. conslaw).
+// Flux in FP64 (eq. conslaw): scalar advection, Euler, or Maxwell in 3D
+// (Sec. 6.1.1: Q(W, e_a) = (-e_a x H, e_a x E), W = (E, H)).
 __device__ static void flux64(const PointArgs& A, const double* W, int a, double* Q)
 {
     if (A.system == kAdvection) {
         Q[0] = A.adv[a] * W[0];
+        return;
+    }
+    if (A.system == kMaxwell) {
+        const int j = (a + 1) % 3, k = (a + 2) % 3;     // e_a x v = v_j e_k - v_k e_j
+        Q[a] = 0.0;
+        Q[k] = -W[3 + j];
+        Q[j] = W[3 + k];
+        Q[3 + a] = 0.0;
+        Q[3 + k] = W[j];
+        Q[3 + j] = -W[k];
         return;
     }
     const int d = A.dim;
@@ -173,7 +184,7 @@ __global__ void init_kernel(PointArgs A, const double* __restrict__ W, T* __rest
     const long long nodes = A.nodes;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
-        double w[5], Q[5];
+        double w[kMaxVars], Q[kMaxVars];
         for (int v = 0; v < A.m; ++v) w[v] = W[v * nodes + i];
         for (int a = 0; a < A.dim; ++a) {
             flux64(A, w, a, Q);
@@ -237,7 +248,7 @@ __global__ void mass_kernel(PointArgs A, const T* __restrict__ f, const double* 
     for (int a = 0; a < A.dim; ++a) nn *= np;
     double vol = 1.0;
     for (int a = 0; a < A.dim; ++a) vol *= A.h[a];
-    double acc[5] = {0, 0, 0, 0, 0};
+    double acc[kMaxVars] = {0, 0, 0, 0, 0, 0};
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
         int id = (int)(i % nn);
@@ -252,7 +263,7 @@ __global__ void mass_kernel(PointArgs A, const T* __restrict__ f, const double* 
             acc[v] += wq * s;
         }
     }
-    block_reduce_store<5>(acc, partial, false);
+    block_reduce_store<kMaxVars>(acc, partial, false);
 }
 
 // Next-step interface defect and iteration residual from the block
@@ -264,7 +275,7 @@ __global__ void defect_kernel(DefectArgs A, const T* __restrict__ sig, const T* 
                               const double* __restrict__ c64, const double* __restrict__ gll,
                               double* __restrict__ partial, double* __restrict__ partial_max)
 {
-    double acc[5] = {0, 0, 0, 0, 0};
+    double acc[kMaxVars] = {0, 0, 0, 0, 0, 0};
     double mx[1] = {0.0};
     const int np = A.degree + 1;
     int tn = 1;
@@ -309,7 +320,7 @@ __global__ void defect_kernel(DefectArgs A, const T* __restrict__ sig, const T* 
         acc[v] += A.dt * A.lambda * fw * (used - actual);
         mx[0] = fmax(mx[0], fabs(used - actual));
     }
-    block_reduce_store<5>(acc, partial, false);
+    block_reduce_store<kMaxVars>(acc, partial, false);
     __syncthreads();
     block_reduce_store<1>(mx, partial_max, true);
 }
@@ -365,7 +376,7 @@ cudaError_t launch_mass(const PointArgs& a, const void* f, const double* gll, do
     const int g = kDiagBlocks;
     if (prec == 1) mass_kernel<float><<<g, kThreads, 0, st>>>(a, (const float*)f, gll, partial);
     else mass_kernel<double><<<g, kThreads, 0, st>>>(a, (const double*)f, gll, partial);
-    finish_kernel<<<1, 32, 0, st>>>(partial, g, 5, 0, out);
+    finish_kernel<<<1, 32, 0, st>>>(partial, g, kMaxVars, 0, out);
     return cudaGetLastError();
 }
 
@@ -374,15 +385,15 @@ cudaError_t launch_defect(const DefectArgs& a, const void* sig, const void* raw,
                           cudaStream_t st)
 {
     const int g = kDiagBlocks;
-    double* pmax = partial + g * 5;
+    double* pmax = partial + g * kMaxVars;
     if (prec == 1)
         defect_kernel<float><<<g, kThreads, 0, st>>>(a, (const float*)sig, (const float*)raw, c64,
                                                      gll, partial, pmax);
     else
         defect_kernel<double><<<g, kThreads, 0, st>>>(a, (const double*)sig, (const double*)raw,
                                                       c64, gll, partial, pmax);
-    finish_kernel<<<1, 32, 0, st>>>(partial, g, 5, 0, out);
-    finish_kernel<<<1, 32, 0, st>>>(pmax, g, 1, 1, out + 5);
+    finish_kernel<<<1, 32, 0, st>>>(partial, g, kMaxVars, 0, out);
+    finish_kernel<<<1, 32, 0, st>>>(pmax, g, 1, 1, out + kMaxVars);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 namespace kin {
 
 constexpr int kMaxNP = 4;          // degree <= 3
+constexpr int kMaxVars = 6;        // conserved variables (Maxwell: E, H)
 constexpr int kDiagBlocks = 304;   // 2 x 152 SMs
 
 struct Inst;
@@ -32,7 +33,7 @@ struct PointArgs {
 struct DefectArgs {
     int dim, degree, m, iters;
     long long total;         // sum of per_pop
-    long long per_pop[30];   // NS[a] * glines[a] for the population's axis
+    long long per_pop[48];   // NS[a] * glines[a] for the population's axis
     long long glines[3];
     long long sig_stride;
     long long raw_stride;

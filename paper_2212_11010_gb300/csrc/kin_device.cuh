@@ -45,6 +45,9 @@ namespace kin {
 
 constexpr int kAdvection = 0;
 constexpr int kEuler = 1;
+constexpr int kMaxwell = 2;        // 3D only: W = (E, H) (Sec. 6.1.1)
+// conserved variables m of a system in D dimensions
+__host__ __device__ constexpr int nvars(int D, int SYS) { return SYS == kAdvection ? 1 : (SYS == kMaxwell ? 6 : D + 2); }
 constexpr int kCoefStride = 32;    // coefficient slots per (axis, sign)
 constexpr int kThreads = 256;      // upper bound on threads per block
 
@@ -97,6 +100,7 @@ struct __align__(16) Inst {
     int stages;              // shared-memory tile buffers per thread block (1 or 2)
     int debug_stall;         // test hook: the load barrier expects 16 bytes that never arrive
     double lambda, gamma, omega;
+    double mu;               // Maxwell: conductivity source factor (1 - sigma dt/2) / (1 + sigma dt/2)
     double adv[3];
     // block-inverse coefficients (computed in FP64 on the device once per
     // context), carried in the launch parameters: read from the constant bank
@@ -233,7 +237,7 @@ __device__ __forceinline__ Line<D, NP, A> line_of(const Inst& I, int line, int o
 template <int D, int P, int SYS, int A>
 __device__ __forceinline__ int items_of_axis(const Inst& I)
 {
-    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    constexpr int M = nvars(D, SYS);
     return 2 * M * (int)I.ax[A].lines.d;
 }
 
@@ -245,7 +249,7 @@ template <int D, int P, int SYS, typename T, int A>
 __device__ __forceinline__ void chain_axis(const Inst& I, int bx, int by, int bz, T* tin)
 {
     constexpr int NP = P + 1;
-    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    constexpr int M = nvars(D, SYS);
     const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
     const int org0 = bx * B0, org1 = by * B1, org2 = bz * B2;
     const int Lp = (int)I.ax[A].lines.d;
@@ -268,7 +272,7 @@ __device__ __forceinline__ void lines_axis(const Inst& I, int bx, int by, int bz
 {
     constexpr int NP = P + 1;
     constexpr int NN = ipow(NP, D);
-    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    constexpr int M = nvars(D, SYS);
     const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
     const int bcells = B0 * B1 * B2;
     const int org0 = bx * B0, org1 = by * B1, org2 = bz * B2;
@@ -381,7 +385,7 @@ __device__ __forceinline__ void relax_block(const Inst& I, T* s, int bcells)
 {
     constexpr int NP = P + 1;
     constexpr int NN = ipow(NP, D);
-    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    constexpr int M = nvars(D, SYS);
     constexpr int NV = 2 * D;
     constexpr int NPOP = NV * M;
     const int nnodes = bcells * NN;
@@ -402,6 +406,45 @@ __device__ __forceinline__ void relax_block(const Inst& I, T* s, int bcells)
 #pragma unroll
             for (int k = 0; k < NV; ++k) acc.add(fk[k * M + v]);
             W[v] = acc.s;
+        }
+        if constexpr (SYS == kMaxwell) {
+            // the Crank-Nicolson conductivity step on W (E <- mu E, H kept),
+            // then the non-equilibrium part relaxed about the new
+            // equilibrium: f <- M(W+) + (1 - omega) (f - M(W-)); the fluxes
+            // are linear, Q(W, e_a) = (-e_a x H, e_a x E) (Sec. 6.1.1)
+            const T mu = T(I.mu), om1 = T(1) - omega;
+            T Wp[M];
+#pragma unroll
+            for (int v = 0; v < M; ++v) Wp[v] = v < 3 ? mu * W[v] : W[v];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int j = (a + 1) % 3, k = (a + 2) % 3;
+                T Qm[M], Qp[M];
+                Qm[a] = T(0);
+                Qm[k] = -W[3 + j];
+                Qm[j] = W[3 + k];
+                Qm[3 + a] = T(0);
+                Qm[3 + k] = W[j];
+                Qm[3 + j] = -W[k];
+                Qp[a] = T(0);
+                Qp[k] = -Wp[3 + j];
+                Qp[j] = Wp[3 + k];
+                Qp[3 + a] = T(0);
+                Qp[3 + k] = Wp[j];
+                Qp[3 + j] = -Wp[k];
+#pragma unroll
+                for (int v = 0; v < M; ++v) {
+                    const T bm = W[v] * inv2d, hm = Qm[v] * inv2l;
+                    const T bp = Wp[v] * inv2d, hp = Qp[v] * inv2l;
+                    T& fp = fk[(2 * a) * M + v];
+                    T& fm = fk[(2 * a + 1) * M + v];
+                    fp = fma(om1, fp - (bm + hm), bp + hp);
+                    fm = fma(om1, fm - (bm - hm), bp - hp);
+                }
+            }
+#pragma unroll
+            for (int pp = 0; pp < NPOP; ++pp) s[pp * pstride + nd] = fk[pp];
+            continue;
         }
         T inv = 0, pr = 0;
         if (SYS == kEuler) {
@@ -462,7 +505,7 @@ template <int D, int P, int SYS, typename T>
 __device__ __forceinline__ void issue_tile_load(const Inst& I, int t, T* s, uint64_t* bar)
 {
     constexpr int NN = ipow(P + 1, D);
-    constexpr int NPOP = 2 * D * (SYS == kAdvection ? 1 : D + 2);
+    constexpr int NPOP = 2 * D * (nvars(D, SYS));
     const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
     const int bcells = B0 * B1 * B2, rowlen = B0 * NN, nrows = B1 * B2, nchunks = NPOP * nrows;
     const TileXYZ c = tile_xyz(I, t);
@@ -485,7 +528,7 @@ template <int D, int P, int SYS, typename T>
 __device__ __forceinline__ void issue_tile_store(const Inst& I, int t, const T* s)
 {
     constexpr int NN = ipow(P + 1, D);
-    constexpr int NPOP = 2 * D * (SYS == kAdvection ? 1 : D + 2);
+    constexpr int NPOP = 2 * D * (nvars(D, SYS));
     const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
     const int bcells = B0 * B1 * B2, rowlen = B0 * NN, nrows = B1 * B2, nchunks = NPOP * nrows;
     const TileXYZ c = tile_xyz(I, t);
@@ -504,7 +547,7 @@ template <int D, int P, int SYS, typename T, bool LOAD>
 __device__ __forceinline__ void copy_tile_generic(const Inst& I, int t, T* s)
 {
     constexpr int NN = ipow(P + 1, D);
-    constexpr int NPOP = 2 * D * (SYS == kAdvection ? 1 : D + 2);
+    constexpr int NPOP = 2 * D * (nvars(D, SYS));
     const int B0 = I.B[0], B1 = D > 1 ? I.B[1] : 1, B2 = D > 2 ? I.B[2] : 1;
     const int bcells = B0 * B1 * B2, rowlen = B0 * NN, nrows = B1 * B2;
     const int nload = NPOP * nrows * rowlen;
@@ -553,7 +596,7 @@ template <int D, int P, int SYS, typename T>
 __global__ void __launch_bounds__(kThreads) step_kernel(const __grid_constant__ Inst I)
 {
     constexpr int NN = ipow(P + 1, D);
-    constexpr int NPOP = 2 * D * (SYS == kAdvection ? 1 : D + 2);
+    constexpr int NPOP = 2 * D * (nvars(D, SYS));
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int flag;

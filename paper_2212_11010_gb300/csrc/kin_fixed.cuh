@@ -28,7 +28,7 @@ struct Shape {
     static constexpr int NP = P + 1;
     static constexpr int NN = ipow(NP, D);
     static constexpr int TN = ipow(NP, D - 1);
-    static constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    static constexpr int M = nvars(D, SYS);
     static constexpr int NPOP = 2 * D * M;
     static constexpr int NROWS = B1 * B2;
     static constexpr int ROWLEN = B0 * NN;

@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(kSxThreads) sx_sweep_kernel(SxArgs S)
 template <int D, int SYS, typename T>
 __global__ void sx_relax_kernel(SxArgs S)
 {
-    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    constexpr int M = nvars(D, SYS);
     constexpr int NV = D + 1;
     T* f = static_cast<T*>(S.f);
     const T omega = T(S.omega);
@@ -539,7 +539,7 @@ __global__ void sx_relax_kernel(SxArgs S)
 template <int D, int SYS, typename T>
 __global__ void sx_init_kernel(SxArgs S, const double* __restrict__ Wd)
 {
-    constexpr int M = SYS == kAdvection ? 1 : D + 2;
+    constexpr int M = nvars(D, SYS);
     constexpr int NV = D + 1;
     T* f = static_cast<T*>(S.f);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S.nodes;

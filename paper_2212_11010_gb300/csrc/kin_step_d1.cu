@@ -14,13 +14,13 @@ static StepKernel pick(int prec)
 
 StepKernel step_kernel_d1(int degree, int system, int prec)
 {
-    switch (degree * 2 + system) {
-    case 2: return pick<1, kAdvection>(prec);
-    case 3: return pick<1, kEuler>(prec);
-    case 4: return pick<2, kAdvection>(prec);
-    case 5: return pick<2, kEuler>(prec);
-    case 6: return pick<3, kAdvection>(prec);
-    case 7: return pick<3, kEuler>(prec);
+    switch (degree * 4 + system) {        // (Maxwell is 3D only)
+    case 4: return pick<1, kAdvection>(prec);
+    case 5: return pick<1, kEuler>(prec);
+    case 8: return pick<2, kAdvection>(prec);
+    case 9: return pick<2, kEuler>(prec);
+    case 12: return pick<3, kAdvection>(prec);
+    case 13: return pick<3, kEuler>(prec);
     default: return nullptr;
     }
 }

@@ -85,13 +85,16 @@ int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3])
 
 StepKernel step_kernel_d3(int degree, int system, int prec)
 {
-    switch (degree * 2 + system) {
-    case 2: return pick<1, kAdvection>(prec);
-    case 3: return pick<1, kEuler>(prec);
-    case 4: return pick<2, kAdvection>(prec);
-    case 5: return pick<2, kEuler>(prec);
-    case 6: return pick<3, kAdvection>(prec);
-    case 7: return pick<3, kEuler>(prec);
+    switch (degree * 4 + system) {
+    case 4: return pick<1, kAdvection>(prec);
+    case 5: return pick<1, kEuler>(prec);
+    case 6: return pick<1, kMaxwell>(prec);
+    case 8: return pick<2, kAdvection>(prec);
+    case 9: return pick<2, kEuler>(prec);
+    case 10: return pick<2, kMaxwell>(prec);
+    case 12: return pick<3, kAdvection>(prec);
+    case 13: return pick<3, kEuler>(prec);
+    case 14: return pick<3, kMaxwell>(prec);
     default: return nullptr;
     }
 }

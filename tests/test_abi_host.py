@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(kin):
 BAD = [
     dict(dim=4), dict(degree=0), dict(degree=4), dict(system=7), dict(lam=-1.0), dict(dt=0.0),
     dict(omega=2.5), dict(omega=0.5), dict(iters=0), dict(precision=9), dict(tiles=(3, 1)),
-    dict(block=(3, 1)), dict(velset=1), dict(gamma=1.0),
+    dict(block=(3, 1)), dict(velset=1), dict(gamma=1.0), dict(system=2),
 ]
 
 
@@ -61,6 +61,21 @@ def test_create_rejects_bad_arguments(kin, bad):
         kin.kin_create(mesh, model, degree, dt, opts)
     assert ei.value.status == kin.KIN_EINVAL
     assert len(kin.kin_last_error(None)) > 0
+
+
+@pytest.mark.parametrize("bad", [dict(sigma=-1.0), dict(sigma=float("nan")), dict(velset=5)],
+                         ids=["sigma<0", "sigma=nan", "D3Q4"])
+def test_create_rejects_bad_maxwell_arguments(kin, bad):
+    # Maxwell's equations run in 3D on the six axis velocities with sigma >= 0
+    velset = bad.pop("velset", 3)
+    mesh, model, opts = kin.make_args(dim=3, n=(4, 4, 4), lo=(0, 0, 0), hi=(1, 1, 1),
+                                      system=kin.KIN_MAXWELL, lam=3.3, omega=2.0, gamma=1.4,
+                                      tiles=(1, 1, 1), iters=3, precision=kin.KIN_FP64,
+                                      block=(0, 0, 0), **bad)
+    model.velset = velset
+    with pytest.raises(kin.KinError) as ei:
+        kin.kin_create(mesh, model, 1, 0.01, opts)
+    assert ei.value.status == kin.KIN_EINVAL
 
 
 def test_null_context_calls_are_rejected(kin):

@@ -24,6 +24,8 @@ not available; these periodic Cartesian problems stand in for them):
   rho = 1 + 0.2 sin(2 pi (x + y + z) + phi), phi ~ U(0, 2 pi), u = (1,1,1),
   p = 1, dt = 5 x the explicit DG limit, 16^3 subdomains.
 * ``densitywave2d`` the 2D analogue on [0,1]^2 (used by the batched mix).
+* ``maxwell3d``    Maxwell's equations on the periodic unit cube, D3Q6, three
+  superposed plane waves, optional uniform conductivity sigma.
 
 Kinetic speed: lambda = 1.1 d max_nodes max_a (|u_a| + c), which keeps the
 2d-velocity equilibria W/(2d) +- Q^a/(2 lambda) monotone.  Explicit DG limit
@@ -39,6 +41,7 @@ import numpy as np
 
 ADVECTION = 0
 EULER = 1
+MAXWELL = 2     # 3D only, W = (E, H)
 
 # Gauss-Lobatto points on [0, 1] (closed forms; Abramowitz & Stegun 25.4.32).
 _GLL = {
@@ -69,10 +72,11 @@ class Workload:
     W0: np.ndarray = field(repr=False)
     exact: Optional[Callable] = field(default=None, repr=False)  # exact(t) -> W
     velset: int = 0           # 0: 2d velocities +-lambda e_a; 1: d + 1 velocities (D2Q3, D3Q4)
+    sigma: float = 0.0        # conductivity (Maxwell only)
 
     @property
     def m(self) -> int:
-        return 1 if self.system == ADVECTION else self.dim + 2
+        return {ADVECTION: 1, EULER: self.dim + 2, MAXWELL: 6}[self.system]
 
     @property
     def nvel(self) -> int:
@@ -94,7 +98,7 @@ class Workload:
         return dict(dim=self.dim, n=self.n, lo=self.lo, hi=self.hi, degree=self.degree,
                     system=self.system, lam=self.lam, dt=self.dt, omega=self.omega,
                     gamma=self.gamma, adv=self.adv, tiles=self.tiles, iters=self.iters,
-                    velset=self.velset)
+                    velset=self.velset, sigma=self.sigma)
 
 
 def node_coords(dim, n, lo, hi, degree) -> np.ndarray:
@@ -244,6 +248,39 @@ def densitywave2d(seed: int = 0, n: int = 64, degree: int = 1, tiles: int = 2, i
                   precision: str = "f32", velset: int = 0) -> Workload:
     return _densitywave(2, seed, n, degree, tiles, iters, dt_mult, omega, steps, precision,
                         velset=velset)
+
+
+def maxwell3d(seed: int = 0, n: int = 64, degree: int = 1, tiles: int = 16, iters: int = 3,
+              dt_mult: float = 5.0, omega: float = 2.0, sigma: float = 0.0, steps: int = 100,
+              precision: str = "f32") -> Workload:
+    """Maxwell (light speed 1) on the periodic unit cube, D3Q6: three plane
+    waves, along x (E_y = H_z), along y (E_z = H_x) and along z (E_x = H_y),
+    each cos(2 pi (s - t) + phi_k) with phases phi_k ~ U(0, 2 pi) and
+    amplitudes ~ U(0.5, 1.5) from the seed; lambda = 3.3 (1.1 d x the light
+    speed); dt = dt_mult x h / ((2p + 1) d).  With sigma = 0 the exact
+    solution is the translated waves; with sigma > 0 there is no closed form
+    here (exact = None)."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.0, 2 * np.pi, size=3)
+    amp = rng.uniform(0.5, 1.5, size=3)
+    lo, hi = (0.0,) * 3, (1.0,) * 3
+    xyz = node_coords(3, (n,) * 3, lo, hi, degree)
+
+    def fields(t):
+        W = np.zeros((6, xyz.shape[0]))
+        # (propagation axis a, E component, H component): E x H points along +e_a
+        for k, (a, e, h) in enumerate(((0, 1, 2), (1, 2, 0), (2, 0, 1))):
+            c = amp[k] * np.cos(2 * np.pi * (xyz[:, a] - t) + phi[k])
+            W[e] += c
+            W[3 + h] += c
+        return W
+
+    h = 1.0 / n
+    dt = dt_mult * h / ((2 * degree + 1) * 3)
+    exact = fields if sigma == 0.0 else None
+    return Workload("maxwell3d", 3, (n,) * 3, lo, hi, degree, MAXWELL, 3.3, dt, omega, 1.4,
+                    (0.0, 0.0, 0.0), _tiles(tiles, 3), iters, steps, precision, fields(0.0), exact,
+                    0, sigma)
 
 
 def with_(w: Workload, **kw) -> Workload:
