@@ -378,6 +378,51 @@ __device__ __forceinline__ TileXYZ tile_xyz(const Inst& I, int t)
     return c;
 }
 
+// Maxwell flux Q(W, e_a) = (-e_a x H, e_a x E) of W = (E, H) (Sec. 6.1.1):
+// with (a, j, k) a cyclic permutation of the axes, e_a x X = (X_j e_k - X_k e_j).
+template <typename V>
+__device__ __forceinline__ void maxwell_flux(const V* W, int a, V* Q, V zero)
+{
+    const int j = (a + 1) % 3, k = (a + 2) % 3;
+    Q[a] = zero;
+    Q[k] = -W[3 + j];
+    Q[j] = W[3 + k];
+    Q[3 + a] = zero;
+    Q[3 + k] = W[j];
+    Q[3 + j] = -W[k];
+}
+
+// Relaxation of one node of Maxwell's equations with a uniform conductivity
+// (Sec. 2.3, Sec. 6.4): the Crank-Nicolson source step on the moments
+// (W+ = (mu E, H)), then the non-equilibrium part relaxed about the new
+// equilibrium, f <- M(W+) + (1 - omega) (f - M(W-)), on the six axis
+// velocities stored as fk[(2a + s) * 6 + v] (s = 0 for +lambda e_a).
+template <typename T>
+__device__ __forceinline__ void maxwell_relax_node(T* fk, const T* W, T mu, T om1, T inv2d, T inv2l)
+{
+    constexpr int M = 6;
+    T Wp[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) Wp[v] = v < 3 ? mu * W[v] : W[v];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T Qm[M], Qp[M];
+        maxwell_flux(W, a, Qm, T(0));
+        maxwell_flux(Wp, a, Qp, T(0));
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            // Q^a has no component along E_a and H_a
+            const bool z = v == a || v == 3 + a;
+            const T bm = W[v] * inv2d, hm = z ? T(0) : Qm[v] * inv2l;
+            const T bp = Wp[v] * inv2d, hp = z ? T(0) : Qp[v] * inv2l;
+            T& fp = fk[(2 * a) * M + v];
+            T& fm = fk[(2 * a + 1) * M + v];
+            fp = fma(om1, fp - (z ? bm : bm + hm), z ? bp : bp + hp);
+            fm = fma(om1, fm - (z ? bm : bm - hm), z ? bp : bp - hp);
+        }
+    }
+}
+
 // Relaxation at every node of the block (eq. over_relaxation) with the 2d
 // velocity equilibria M_{a,+-} = W/(2d) +- Q^a(W)/(2 lambda).
 template <int D, int P, int SYS, typename T>
@@ -408,40 +453,7 @@ __device__ __forceinline__ void relax_block(const Inst& I, T* s, int bcells)
             W[v] = acc.s;
         }
         if constexpr (SYS == kMaxwell) {
-            // the Crank-Nicolson conductivity step on W (E <- mu E, H kept),
-            // then the non-equilibrium part relaxed about the new
-            // equilibrium: f <- M(W+) + (1 - omega) (f - M(W-)); the fluxes
-            // are linear, Q(W, e_a) = (-e_a x H, e_a x E) (Sec. 6.1.1)
-            const T mu = T(I.mu), om1 = T(1) - omega;
-            T Wp[M];
-#pragma unroll
-            for (int v = 0; v < M; ++v) Wp[v] = v < 3 ? mu * W[v] : W[v];
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                const int j = (a + 1) % 3, k = (a + 2) % 3;
-                T Qm[M], Qp[M];
-                Qm[a] = T(0);
-                Qm[k] = -W[3 + j];
-                Qm[j] = W[3 + k];
-                Qm[3 + a] = T(0);
-                Qm[3 + k] = W[j];
-                Qm[3 + j] = -W[k];
-                Qp[a] = T(0);
-                Qp[k] = -Wp[3 + j];
-                Qp[j] = Wp[3 + k];
-                Qp[3 + a] = T(0);
-                Qp[3 + k] = Wp[j];
-                Qp[3 + j] = -Wp[k];
-#pragma unroll
-                for (int v = 0; v < M; ++v) {
-                    const T bm = W[v] * inv2d, hm = Qm[v] * inv2l;
-                    const T bp = Wp[v] * inv2d, hp = Qp[v] * inv2l;
-                    T& fp = fk[(2 * a) * M + v];
-                    T& fm = fk[(2 * a + 1) * M + v];
-                    fp = fma(om1, fp - (bm + hm), bp + hp);
-                    fm = fma(om1, fm - (bm - hm), bp - hp);
-                }
-            }
+            maxwell_relax_node(fk, W, T(I.mu), T(1) - omega, inv2d, inv2l);
 #pragma unroll
             for (int pp = 0; pp < NPOP; ++pp) s[pp * pstride + nd] = fk[pp];
             continue;

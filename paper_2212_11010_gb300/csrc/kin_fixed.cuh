@@ -568,6 +568,12 @@ __device__ __forceinline__ void fixed_relax(const Inst& I, T* s)
             for (int kk = 0; kk < NV; ++kk) acc.add(fk[kk * M + v]);
             W[v] = acc.s;
         }
+        if constexpr (SYS == kMaxwell) {
+            maxwell_relax_node(fk, W, T(I.mu), T(1) - omega, inv2d, inv2l);
+#pragma unroll
+            for (int pp = 0; pp < NPOP; ++pp) s[pp * S::PSTR + o] = fk[pp];
+            continue;
+        }
         T inv = 0, pr = 0;
         if (SYS == kEuler) {
             inv = T(1) / W[0];
@@ -674,6 +680,36 @@ __device__ __forceinline__ void fixed_relax_pairs(const Inst& I, float* s)
                 sum = t;
             }
             W[v] = sum;
+        }
+        if constexpr (SYS == kMaxwell) {
+            // maxwell_relax_node on node pairs
+            const float2 mu = f2((float)I.mu), zero = f2(0.0f);
+            auto neg2 = [](float2 x) { return make_float2(-x.x, -x.y); };
+            float2 Wp[M];
+#pragma unroll
+            for (int v = 0; v < M; ++v) Wp[v] = v < 3 ? mul2(mu, W[v]) : W[v];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int j = (a + 1) % 3, kk = (a + 2) % 3;
+                float2 Qm[M], Qp[M];
+                Qm[a] = zero; Qm[kk] = neg2(W[3 + j]); Qm[j] = W[3 + kk];
+                Qm[3 + a] = zero; Qm[3 + kk] = W[j]; Qm[3 + j] = neg2(W[kk]);
+                Qp[a] = zero; Qp[kk] = neg2(Wp[3 + j]); Qp[j] = Wp[3 + kk];
+                Qp[3 + a] = zero; Qp[3 + kk] = Wp[j]; Qp[3 + j] = neg2(Wp[kk]);
+#pragma unroll
+                for (int v = 0; v < M; ++v) {
+                    const bool z = v == a || v == 3 + a;
+                    const float2 bm = mul2(W[v], inv2d), bp = mul2(Wp[v], inv2d);
+                    const float2 hm = z ? zero : mul2(Qm[v], inv2l), hp = z ? zero : mul2(Qp[v], inv2l);
+                    const int ip = (2 * a) * M + v, im = (2 * a + 1) * M + v;
+                    const float2 fp = get(ip), fm = get(im);
+                    const float2 np_ = fma2(omc, sub2(fp, z ? bm : add2(bm, hm)), z ? bp : add2(bp, hp));
+                    const float2 nm_ = fma2(omc, sub2(fm, z ? bm : sub2(bm, hm)), z ? bp : sub2(bp, hp));
+                    *reinterpret_cast<float2*>(s + ip * S::PSTR + o) = np_;
+                    *reinterpret_cast<float2*>(s + im * S::PSTR + o) = nm_;
+                }
+            }
+            continue;
         }
         float2 inv = f2(0.0f), pres = f2(0.0f);
         if (SYS == kEuler) {

@@ -1,5 +1,5 @@
 // kin_step_d3.cu -- instantiations of the fused sweep + relaxation kernel for
-// 3 space dimension(s), degrees 1..3, scalar advection and Euler, FP32/FP64.
+// 3 space dimension(s), degrees 1..3, scalar advection, Euler and Maxwell, FP32/FP64.
 #include "kin_aux.h"
 #include "kin_device.cuh"
 #include "kin_fixed.cuh"
@@ -20,7 +20,12 @@ static StepKernel pick(int prec)
     X(1, kEuler, float, 8, 2, 2, 128, 6, 3)         \
     X(1, kEuler, float, 4, 4, 2, 128, 6, 3)         \
     X(1, kEuler, float, 8, 4, 2, 256, 3, 1)         \
-    X(1, kEuler, float, 4, 4, 4, 320, 3, 1)
+    X(1, kEuler, float, 4, 4, 4, 320, 3, 1)         \
+    X(1, kMaxwell, float, 4, 4, 2, 128, 4, 2)       \
+    X(1, kMaxwell, float, 8, 2, 2, 128, 4, 2)       \
+    X(1, kMaxwell, float, 4, 2, 2, 64, 8, 4)        \
+    X(1, kMaxwell, float, 8, 4, 2, 256, 2, 1)       \
+    X(1, kMaxwell, float, 4, 4, 4, 256, 2, 1)
 
 FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3], int stages)
 {
@@ -61,6 +66,15 @@ int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3])
             ++n;
         }
     };
+    if (system == kMaxwell) {
+        if (dim == 3 && prec == 1 && degree == 1) {
+            add(4, 4, 4);
+            add(4, 4, 2);
+            add(8, 2, 2);
+            add(4, 2, 2);
+        }
+        return n;
+    }
     if (system != kEuler) return 0;
     if (dim == 2 && prec == 1) {
         if (degree == 1) {

@@ -25,14 +25,17 @@ def kin():
 def _mix():
     # uneven 2D Euler problems (degrees 1..3, n 32..128, 32-cell subdomains),
     # plus members without a fixed-shape kernel (3D, FP64 p = 1, odd block)
+    # and Maxwell members with and without one
     ws = [workloads.vortex2d(seed=1, n=64, degree=2, tiles=2, dt_mult=6.0),
           workloads.densitywave2d(seed=2, n=32, degree=1, tiles=1, dt_mult=3.0),
           workloads.vortex2d(seed=3, n=128, degree=3, tiles=4, dt_mult=7.0),
           workloads.vortex2d(seed=4, n=96, degree=2, tiles=3, dt_mult=2.0),
           workloads.densitywave2d(seed=5, n=64, degree=1, tiles=2, dt_mult=8.0),
           workloads.densitywave3d(seed=6, n=16, degree=1, tiles=2, dt_mult=5.0),
-          workloads.vortex2d(seed=7, n=32, degree=1, tiles=1, dt_mult=4.0, precision="f64")]
-    blocks = [None, None, None, None, (16, 4), None, None]
+          workloads.vortex2d(seed=7, n=32, degree=1, tiles=1, dt_mult=4.0, precision="f64"),
+          workloads.maxwell3d(seed=8, n=16, degree=1, tiles=2, dt_mult=6.0, sigma=2.0),
+          workloads.maxwell3d(seed=9, n=8, degree=2, tiles=1, dt_mult=4.0, sigma=0.5)]
+    blocks = [None, None, None, None, (16, 4), None, None, None, None]
     return ws, blocks
 
 

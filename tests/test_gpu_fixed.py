@@ -14,6 +14,8 @@ SHAPES = [
     (2, 1, "f32", (16, 8)), (2, 1, "f32", (16, 16)), (2, 2, "f32", (8, 8)), (2, 3, "f32", (8, 4)),
     (2, 3, "f32", (8, 8)), (2, 2, "f64", (8, 8)),
     (3, 1, "f32", (8, 2, 2)), (3, 1, "f32", (4, 4, 2)), (3, 1, "f32", (8, 4, 2)), (3, 1, "f32", (4, 4, 4)),
+    (3, 1, "f32", (4, 4, 2), "maxwell"), (3, 1, "f32", (8, 2, 2), "maxwell"),
+    (3, 1, "f32", (4, 2, 2), "maxwell"), (3, 1, "f32", (8, 4, 2), "maxwell"), (3, 1, "f32", (4, 4, 4), "maxwell"),
 ]
 
 
@@ -29,7 +31,11 @@ def kin():
     return kin
 
 
-def _problem(dim, degree, prec, block):
+def _problem(dim, degree, prec, block, system="euler"):
+    if system == "maxwell":
+        w = workloads.maxwell3d(seed=6, n=16, degree=degree, tiles=2, dt_mult=30.0, sigma=3.0, omega=1.8,
+                                precision=prec)
+        return workloads.with_(w, tiles=(2, 2, 2))
     if dim == 2:
         n = 2 * max(block) * 2
         w = workloads.vortex2d(seed=5, n=n, degree=degree, tiles=2, dt_mult=40.0, precision=prec)
@@ -47,8 +53,8 @@ def _run(kin, w, block, steps, threads=0, stages=0):
 
 @pytest.mark.parametrize("shape", SHAPES, ids=[str(s) for s in SHAPES])
 def test_fixed_shape_matches_oracle_and_generic(kin, shape):
-    dim, degree, prec, block = shape
-    w = _problem(dim, degree, prec, block)
+    dim, degree, prec, block = shape[:4]
+    w = _problem(*shape)
     steps = 4
     W, f, info = _run(kin, w, block, steps)
     assert info.specialised == 1 and tuple(info.block[:dim]) == tuple(block)
