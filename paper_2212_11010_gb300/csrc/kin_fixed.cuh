@@ -474,7 +474,7 @@ __device__ __forceinline__ void chain_setup(const Inst& I, int hid, int sgn, int
 }
 
 // Look-back inflows of all lines of this thread (every axis of its sign),
-// folded while the tile's copies fly.  The walks of all axes advance
+// folded before the tile's copies are issued.  The walks of all axes advance
 // together one summary block per step: every line keeps the 32-bit element
 // index of its next summary, which moves by the line count of its axis and
 // wraps (periodically) after the last block; the unrolled steps let the
@@ -839,8 +839,8 @@ __device__ __forceinline__ void fixed_chain_tile(const Inst& I, int t, T* tin)
 }
 
 // Fixed-shape step kernel on a persistent grid (blocks walk tiles
-// blockIdx.x + k gridDim.x).  With STG = 1 a tile is loaded, its look-back
-// inflows folded while the copies fly, then computed.  With STG = 2 the
+// blockIdx.x + k gridDim.x).  With STG = 1 a tile's look-back inflows are
+// folded, then its copies issued and waited for, then it is computed.  With STG = 2 the
 // block owns two tile buffers: the next tile's copies are issued before the
 // current tile is computed, so loads of one tile overlap the work on the
 // previous one.
@@ -858,8 +858,11 @@ __global__ void __launch_bounds__(NTH, MINB) step_kernel_fixed(const __grid_cons
     if (STG == 2) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, t, s0);
     for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
         T* const cur = (i & 1) ? s1 : s0;
-        if (STG == 1) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, t, cur);
+        // (one buffer: the look-back first, so that its summary loads do not
+        // queue behind the tile's copies; the other resident blocks keep
+        // HBM busy meanwhile)
         if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH>(I, t, tin);
+        if (STG == 1) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, t, cur);
         const int tn = t + gridDim.x;
         if (STG == 2 && tn < ntiles) {
             fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, tn, (i & 1) ? s0 : s1);
@@ -892,8 +895,8 @@ __global__ void __launch_bounds__(NTH, MINB)
     for (int i = 0; w < nwork; ++i, w += gridDim.x) {
         const Inst& I = insts[wk.x];
         T* const cur = (i & 1) ? s1 : s0;
-        if (STG == 1) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, wk.y, cur);
         if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH>(I, wk.y, tin);
+        if (STG == 1) fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, wk.y, cur);
         const int wn = w + gridDim.x;
         int2 wkn = wk;
         if (wn < nwork) wkn = work[wn];

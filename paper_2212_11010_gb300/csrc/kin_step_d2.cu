@@ -21,7 +21,7 @@ static StepKernel pick(int prec)
     X(1, kEuler, float, 16, 16, 256, 3, 1)        \
     X(2, kEuler, float, 8, 8, 192, 5, 3)          \
     X(3, kEuler, float, 8, 4, 128, 6, 3)          \
-    X(3, kEuler, float, 8, 8, 128, 3, 1)          \
+    X(3, kEuler, float, 8, 8, 256, 3, 1)          \
     X(2, kEuler, double, 8, 8, 192, 3, 1)
 
 FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3], int stages)

@@ -51,8 +51,8 @@ FixedKernel fixed_kernel_d3(int degree, int system, int prec, const int B[3], in
 }
 
 // One tile buffer: the two-buffer schedule halves the resident blocks, and
-// with the look-back folded while the copies fly the loads are already hidden
-// behind the other blocks' work (measured slower for every compiled shape).
+// the loads of one block are already hidden behind the other blocks' work
+// (measured slower for every compiled shape).
 int fixed_default_stages(int, int, int, int, const int*) { return 1; }
 
 int fixed_shapes(int dim, int degree, int system, int prec, int out[4][3])
