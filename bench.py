@@ -66,7 +66,7 @@ def flops_per_dof(dim, degree, m, nvel, maxwell=False):
 # DRAM bytes (read + write) of one step launch from an ncu capture of the same
 # kernel and workload (profiles/step_kernel_fixed_vortex2d_256x256_p2.md);
 # stores still in L2 at kernel end are not counted by the capture.
-NCU_TRAFFIC = {("vortex2d", "f32"): 39.759616e6 + 0.075776e6}
+NCU_TRAFFIC = {}
 
 
 def make_workload(name):
@@ -86,6 +86,9 @@ def make_workload(name):
     elif name == "densitywave3d-d3q4":
         w = workloads.densitywave3d(seed=0, velset=1)
         desc = "densitywave3d-euler-128^3-p1-D3Q4-16^3sub-K3"
+    elif name == "vortex2d-512-p3":
+        w = workloads.with_(workloads.vortex2d(seed=0, n=512, degree=3), tiles=(16, 16))
+        desc = "vortex2d-euler-512x512-p3-D2Q4-16x16sub-K3"
     elif name == "maxwell3d":
         w = workloads.maxwell3d(seed=0, n=128, degree=1, tiles=16, sigma=1.0)
         desc = "maxwell3d-128^3-p1-D3Q6-16^3sub-K3-sigma1"
@@ -532,7 +535,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="vortex2d",
                     choices=["vortex2d", "densitywave3d", "advection1d", "batched", "serving",
-                             "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d"])
+                             "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d", "vortex2d-512-p3"])
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
