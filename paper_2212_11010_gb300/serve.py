@@ -43,11 +43,34 @@ def state_bytes_estimate(w, esize=4) -> int:
 
 class Server:
     def __init__(self, budget_bytes: float = 150e9, chunk_steps: int = 25, torch_alloc: bool = True,
-                 keep_results: bool = True):
+                 keep_results: bool = True, pinned_results: bool = True):
         self.budget = float(budget_bytes)
         self.chunk = int(chunk_steps)
         self.torch_alloc = torch_alloc
         self.keep_results = keep_results
+        # results are read back into page-locked host buffers (reused by size
+        # when the caller does not keep them), so the device-to-host copy runs
+        # at the link's rate instead of through the driver's staging copies
+        self.pinned_results = pinned_results
+        self._pool = {}
+
+    def _result_buffer(self, n):
+        free = self._pool.setdefault(n, [])
+        if free:
+            return free.pop()
+        import torch
+        return torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+
+    def _read_result(self, ctx):
+        n = ctx.info.state_values
+        if not self.pinned_results:
+            return ctx.get_state()
+        buf = self._result_buffer(n)
+        ctx.get_state(buf)
+        if self.keep_results:
+            return buf                                  # handed to the caller
+        self._pool[n].append(buf)
+        return None
 
     def run(self, requests, workload_of, clock=time.perf_counter):
         """requests: objects with rid, arrival (s), steps; workload_of(r) -> Workload.
@@ -105,7 +128,7 @@ class Server:
                     a[2] -= k
                     if a[2] == 0:
                         rec, ctx = a[0], a[1]
-                        W = ctx.get_state()
+                        W = self._read_result(ctx)
                         rec.finished = clock() - t0
                         if self.keep_results:
                             rec.result = W
