@@ -64,9 +64,11 @@ def flops_per_dof(dim, degree, m, nvel, maxwell=False):
         relax = m * (nvel - 1) + (1 + 2 * dim + 4) + dim * (1 + 2 * dim + 3 + m * 8)
     return sweep + summary + relax / npop + 1.0
 # DRAM bytes (read + write) of one step launch from an ncu capture of the same
-# kernel and workload (profiles/step_kernel_fixed_vortex2d_256x256_p2.md);
-# stores still in L2 at kernel end are not counted by the capture.
-NCU_TRAFFIC = {}
+# kernel and workload (profiles/step_kernel_fixed_vortex2d_256x256_p2.md,
+# profiles/step_kernel_fixed_vortex2d_512x512_p3.md); stores still in L2 at
+# kernel end are not counted by the capture.
+NCU_TRAFFIC = {("vortex2d", "f32"): 39.759616e6 + 0.024e6,
+               ("vortex2d-512-p3", "f32"): 279.486976e6 + 220.965376e6}
 
 
 def make_workload(name):
