@@ -80,12 +80,19 @@ class Server:
         the requests that have arrived meanwhile (context creation and
         initial state run on the new contexts' own streams while the chunk
         runs), then waits for the chunk, retires finished requests and folds
-        the admitted ones into the next batch."""
+        the admitted ones into the next batch.  After the run,
+        self.device_busy_s holds the device time spent inside chunks."""
+        import torch
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         records = {r.rid: Served(r.rid, r.arrival) for r in requests}
         active = []            # [record, context, remaining steps, bytes]
         used = 0.0
         batch = None
+        # the batch runs on the server's stream; new contexts are created and
+        # loaded on a second stream, so admission overlaps the running chunk
+        run_stream = torch.cuda.Stream()
+        adm_stream = torch.cuda.Stream()
+        chunks = []            # (start, end) events of every chunk on the run stream
         t0 = clock()
 
         def admit(now):
@@ -98,7 +105,8 @@ class Server:
                 if used + need > self.budget and (active or new):
                     break                                  # wait for memory to free up
                 pending.popleft()
-                ctx = Context.from_workload(w, precision=KIN_FP32, torch_alloc=self.torch_alloc)
+                ctx = Context.from_workload(w, precision=KIN_FP32, torch_alloc=self.torch_alloc,
+                                            stream=adm_stream.cuda_stream)
                 ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
                 rec = records[r.rid]
                 rec.admitted = clock() - t0
@@ -113,9 +121,13 @@ class Server:
             if active:
                 if batch is None:
                     # membership changes every few chunks: direct launches, no graph capture
-                    batch = Batch([a[1] for a in active], graphs=False)
+                    batch = Batch([a[1] for a in active], stream=run_stream.cuda_stream, graphs=False)
                 k = min(self.chunk, min(a[2] for a in active))
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record(run_stream)
                 batch.step(k)                              # asynchronous
+                ev[1].record(run_stream)
+                chunks.append(ev)
             new = admit(clock() - t0)                      # overlaps the chunk
             if not active and not new:
                 if pending:
@@ -147,10 +159,14 @@ class Server:
             active = still + new
         if batch is not None:
             batch.close()
+        torch.cuda.synchronize()
+        # device time spent inside chunks (the rest of the makespan is host
+        # work between chunks, ramp-up and tail)
+        self.device_busy_s = sum(a.elapsed_time(b) for a, b in chunks) * 1e-3
         return [records[r.rid] for r in requests]
 
 
-def summarize(records):
+def summarize(records, device_busy_s=None):
     lat = np.array([r.latency for r in records])
     t_first = min(r.arrival for r in records)
     t_last = max(r.finished for r in records)
@@ -158,4 +174,6 @@ def summarize(records):
     return {"requests": len(records), "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
             "makespan_s": t_last - t_first, "dof_updates": work,
-            "dof_updates_per_s": work / (t_last - t_first)}
+            "dof_updates_per_s": work / (t_last - t_first),
+            "device_busy_s": device_busy_s,
+            "dof_updates_per_device_s": work / device_busy_s if device_busy_s else None}
