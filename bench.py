@@ -440,7 +440,7 @@ def run_batched(args):
     batch.sync()
     with ClockSampler(0) as clk:
         t0 = time.perf_counter()
-        el = _events_time(stream, lambda: batch.step(1), args.steps)
+        el = _events_time(stream, lambda: batch.step(args.steps), 1)   # K steps in one call
         clk.mark(t0, time.perf_counter())
     batch.sync()
     value = dofs * args.steps / el
