@@ -66,6 +66,8 @@ class _Problem(ctypes.Structure):
         ("iters", ctypes.c_int),
         ("velset", ctypes.c_int),
         ("sigma", ctypes.c_double),
+        ("inflow", ctypes.c_int * 3),
+        ("Wb", ctypes.c_double * (3 * 2 * 6)),
     ]
 
 
@@ -132,6 +134,8 @@ class Problem:
     iters: int = 3
     velset: int = AXIS
     sigma: float = 0.0
+    inflow: tuple = (0, 0, 0)      # 1: axis a has inflow boundaries instead of being periodic
+    Wb: object = None              # boundary states, array (3 axes, 2 faces, m) (lower, upper face)
     _c: _Problem = field(default=None, repr=False, compare=False)
 
     def c(self) -> _Problem:
@@ -154,6 +158,12 @@ class Problem:
         p.iters = self.iters
         p.velset = self.velset
         p.sigma = self.sigma
+        p.inflow = (ctypes.c_int * 3)(*pad(self.inflow, 0))
+        wb = np.zeros((3, 2, 6))
+        if self.Wb is not None:
+            a = np.asarray(self.Wb, dtype=float)
+            wb[:a.shape[0], :, :a.shape[2]] = a
+        p.Wb = (ctypes.c_double * 36)(*wb.reshape(-1))
         self._c = p
         return p
 

@@ -30,6 +30,12 @@
  *   - On a periodic domain a subdomain's face at its own box boundary is an
  *     interface face even when the neighbour across it is itself (one
  *     subdomain couples to itself through the periodic wrap).
+ *   - Inflow boundaries (axes with inflow[a] = 1): the paper prescribes the
+ *     solution on the domain boundary (Sec. 6.2) and upwinds with the cell
+ *     across each face (eq. dg_imp); at a domain boundary the value across
+ *     the face is the Maxwellian M_k(Wb) of the face's boundary state.  It is
+ *     data, the same in every subdomain iteration, and such faces are not
+ *     interfaces (no mass defect).
  *
  * parity pinned: see tests/test_oracle_*.py (closed forms, dense global
  * assembly, dense block-Jacobi assembly, conservation, exact solutions).
@@ -71,6 +77,10 @@ static int check_problem(const ko_problem* P)
     if (!(P->lambda > 0) || !(P->dt > 0)) return -8;
     if (P->iters < 0) return -9;
     if (P->velset != KO_AXIS && P->velset != KO_SIMPLEX) return -10;
+    for (int a = 0; a < 3; ++a) {
+        if (P->inflow[a] != 0 && P->inflow[a] != 1) return -11;
+        if (P->inflow[a] && (a >= P->dim || P->velset != KO_AXIS)) return -11;
+    }
     return 0;
 }
 
@@ -464,6 +474,7 @@ typedef struct {
     int face_lo[3][KO_MAXNN];     /* node lies on the face at x_a = lower   */
     int face_hi[3][KO_MAXNN];     /* node lies on the face at x_a = upper   */
     int acr[3][KO_MAXNN];         /* matching node of the neighbour cell    */
+    double bval[3][2];            /* inflow value M_k(Wb)[v] of face (axis, lower/upper) */
 } pop_ctx;
 
 static void fill_node_tables(pop_ctx* C)
@@ -500,11 +511,18 @@ static void solve_cell(const pop_ctx* C, const int c[3], const double* fn,
             if (!(vn < 0)) continue;              /* inflow faces only */
             int nb[3] = {c[0], c[1], c[2]};
             nb[a] = (c[a] + side + P->n[a]) % P->n[a];
+            const int* on_face = (side < 0) ? C->face_lo[a] : C->face_hi[a];
+            if (P->inflow[a] && c[a] + side != nb[a]) {
+                /* domain boundary: the prescribed Maxwellian */
+                const double fb = C->bval[a][side < 0 ? 0 : 1];
+                for (int i = 0; i < nn; ++i)
+                    if (on_face[i]) b[i] += tau * (-vn) * C->facew[a][i] * fb;
+                continue;
+            }
             int boundary = (side < 0) ? (c[a] % C->L[a] == 0)
                                       : (c[a] % C->L[a] == C->L[a] - 1);
             const double* src = boundary ? prev : cur;
             size_t nbase = cell_id(P, nb) * nn;
-            const int* on_face = (side < 0) ? C->face_lo[a] : C->face_hi[a];
             for (int i = 0; i < nn; ++i) {
                 if (!on_face[i]) continue;
                 b[i] += tau * (-vn) * C->facew[a][i] * src[nbase + C->acr[a][i]];
@@ -560,6 +578,7 @@ static double interface_defect(const pop_ctx* C, const double* prev, const doubl
                         if (!boundary) continue;
                         int nb[3] = {c[0], c[1], c[2]};
                         nb[a] = (c[a] + side + P->n[a]) % P->n[a];
+                        if (P->inflow[a] && c[a] + side != nb[a]) continue;   /* domain boundary */
                         size_t nbase = cell_id(P, nb) * nn;
                         const int* on_face = (side < 0) ? C->face_lo[a] : C->face_hi[a];
                         for (int i = 0; i < nn; ++i) {
@@ -572,13 +591,23 @@ static double interface_defect(const pop_ctx* C, const double* prev, const doubl
     return acc;
 }
 
-static int transport_population(const ko_problem* P, int k, double* f, double* defect,
+static int transport_population(const ko_problem* P, int k, int v, double* f, double* defect,
                                 int* iters_done)
 {
     pop_ctx C;
     double xi[KO_MAXNP];
     C.P = P;
     C.k = k;
+    for (int a = 0; a < 3; ++a)
+        for (int sd = 0; sd < 2; ++sd) {
+            C.bval[a][sd] = 0.0;
+            if (a < P->dim && P->inflow[a]) {
+                double M[4 * KO_MAXM * 2];
+                int rc = ko_maxwellian(P, P->Wb[a][sd], M);
+                if (rc) return rc;
+                C.bval[a][sd] = M[k * ko_num_vars(P) + v];
+            }
+        }
     C.nn = nodes_per_cell(P);
     velocity(P, k, C.V);
     ko_gll(P->degree, xi, C.w);
@@ -639,7 +668,7 @@ int ko_transport(const ko_problem* P, double* f, double* defect, int* iters_done
         for (int v = 0; v < m; ++v) {
             double dfc = 0.0;
             int done = 0;
-            rc = transport_population(P, k, f + (size_t)(k * m + v) * nodes, &dfc, &done);
+            rc = transport_population(P, k, v, f + (size_t)(k * m + v) * nodes, &dfc, &done);
             if (rc) return rc;
             if (defect) defect[v] += dfc;
             if (done > maxdone) maxdone = done;

@@ -35,6 +35,7 @@ extern "C" {
 #endif
 
 enum { KO_ADVECTION = 0, KO_EULER = 1, KO_MAXWELL = 2 };
+#define KO_MAXM 6       /* most conserved variables of a system (Maxwell)       */
 enum { KO_AXIS = 0, KO_SIMPLEX = 1 };
 
 typedef struct {
@@ -53,6 +54,12 @@ typedef struct {
     int iters;          /* subdomain iterations K (>= 1); 0 = to fixed point  */
     int velset;         /* KO_AXIS (2d velocities) or KO_SIMPLEX (d + 1)      */
     double sigma;       /* conductivity (Maxwell only; uniform), >= 0         */
+    int inflow[3];      /* 0: axis a periodic; 1: both faces of axis a are
+                           domain boundaries where the incoming populations
+                           take the Maxwellian of the face state Wb (axis
+                           velocity sets only)                                */
+    double Wb[3][2][KO_MAXM];  /* boundary state of face (axis, 0 = lower,
+                                  1 = upper), constant in time              */
 } ko_problem;
 
 int    ko_num_vars(const ko_problem* P);          /* m                      */

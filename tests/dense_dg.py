@@ -13,6 +13,11 @@ different route from the oracle's Newton iteration and product formula.
 * ``block_jacobi``  the subdomain iteration of eq. ibvp in matrix form: the
                     couplings across subdomain-boundary faces (K_out) use the
                     previous iterate, x^0 = f^n, K iterations.
+
+With ``inflow[a] = 1`` axis a is not periodic: a face on the domain boundary
+couples to a prescribed boundary value instead of the cell across the wrap.
+``assemble_bc`` returns those couplings per face, and the solves take the
+boundary values as a known right-hand side.
 """
 import numpy as np
 
@@ -43,6 +48,14 @@ def lagrange_derivative(xi):
 def assemble(dim, n, lo, hi, p, V, tiles):
     """Return (M, K, Kout): mass (diagonal), full transport operator and the
     part of K that couples across subdomain-boundary faces."""
+    M, K, Kout, _ = assemble_bc(dim, n, lo, hi, p, V, tiles, (0, 0, 0))
+    return M, K, Kout
+
+
+def assemble_bc(dim, n, lo, hi, p, V, tiles, inflow):
+    """(M, K, Kout, Kb): as ``assemble``, plus Kb[(a, side)], the coupling of
+    every node to the boundary value of face (axis a, side -1 lower / +1
+    upper) of the axes with inflow[a] = 1, where K has no coupling."""
     xi, w = gll_numpy(p)
     Dl = lagrange_derivative(xi)
     npn = p + 1
@@ -56,6 +69,8 @@ def assemble(dim, n, lo, hi, p, V, tiles):
     M = np.zeros(N)
     K = np.zeros((N, N))
     Kout = np.zeros((N, N))
+    Kb = {}
+    inflow = tuple(inflow) + (0,) * (3 - len(inflow))
     vol = np.prod(h)
 
     def nidx(ix):
@@ -97,6 +112,9 @@ def assemble(dim, n, lo, hi, p, V, tiles):
                             elif vn < 0:
                                 nb = list(c)
                                 raw = c[a] + side
+                                if inflow[a] and (raw < 0 or raw >= n[a]):
+                                    Kb.setdefault((a, side), np.zeros(N))[gi] += vn * fw
+                                    continue
                                 nb[a] = raw % n[a]
                                 jj = list(ii)
                                 jj[a] = p if side < 0 else 0
@@ -106,18 +124,26 @@ def assemble(dim, n, lo, hi, p, V, tiles):
                                 K[gi, gj] += vn * fw
                                 if crosses:
                                     Kout[gi, gj] += vn * fw
-    return M, K, Kout
+    return M, K, Kout, Kb
 
 
-def global_cn(M, K, tau, fn):
+def _boundary_rhs(Kb, bvals, N):
+    r = np.zeros(N)
+    for face, col in (Kb or {}).items():
+        r += col * bvals[face]
+    return r
+
+
+def global_cn(M, K, tau, fn, Kb=None, bvals=None):
     A = np.diag(M) + tau * K
-    fstar = np.linalg.solve(A, M * fn)
+    fstar = np.linalg.solve(A, M * fn - tau * _boundary_rhs(Kb, bvals, len(fn)))
     return 2.0 * fstar - fn
 
 
-def block_jacobi(M, K, Kout, tau, fn, iters):
+def block_jacobi(M, K, Kout, tau, fn, iters, Kb=None, bvals=None):
     Ain = np.diag(M) + tau * (K - Kout)
+    rb = tau * _boundary_rhs(Kb, bvals, len(fn))
     x = fn.copy()
     for _ in range(iters):
-        x = np.linalg.solve(Ain, M * fn - tau * (Kout @ x))
+        x = np.linalg.solve(Ain, M * fn - tau * (Kout @ x) - rb)
     return 2.0 * x - fn

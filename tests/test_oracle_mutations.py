@@ -50,11 +50,16 @@ MUTATIONS = {
     "maxwell_source_damps_h": ("Wp[v] = v < 3 ? mu * W[v] : W[v];", "Wp[v] = mu * W[v];"),
     "maxwell_literal_relaxation": ("*fp = Mp[pop] + (1.0 - P->omega) * (*fp - M[pop]);",
                                    "*fp = P->omega * Mp[pop] + (1.0 - P->omega) * (*fp);"),
+    "inflow_face_swapped": ("C->bval[a][side < 0 ? 0 : 1]", "C->bval[a][side < 0 ? 1 : 0]"),
+    "inflow_axis_wraps": ("if (P->inflow[a] && c[a] + side != nb[a]) {",
+                          "if (P->inflow[a] && c[a] + side != nb[a] && 0) {"),
+    "inflow_value_first_variable": ("C.bval[a][sd] = M[k * ko_num_vars(P) + v];",
+                                    "C.bval[a][sd] = M[k * ko_num_vars(P)];"),
 }
 
 PIN_FILES = ["tests/test_oracle_basis.py", "tests/test_oracle_relaxation.py",
              "tests/test_oracle_transport.py", "tests/test_oracle_simplex.py",
-             "tests/test_oracle_maxwell.py"]
+             "tests/test_oracle_maxwell.py", "tests/test_oracle_inflow.py"]
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
