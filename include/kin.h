@@ -71,13 +71,18 @@ enum { KIN_ADVECTION = 0, KIN_EULER = 1, KIN_MAXWELL = 2 };
 enum { KIN_D1Q2 = 1, KIN_D2Q4 = 2, KIN_D3Q6 = 3, KIN_D2Q3 = 4, KIN_D3Q4 = 5 };
 enum { KIN_FP64 = 0, KIN_FP32 = 1 };                /* kin_opts.precision */
 
-/* Periodic Cartesian box [lo, hi] with n[a] cells along axis a (axes >= dim
- * must have n = 1). */
+/* Cartesian box [lo, hi] with n[a] cells along axis a (axes >= dim must have
+ * n = 1).  inflow[a] = 0: axis a is periodic; inflow[a] = 1: both faces of
+ * axis a are domain boundaries where the populations entering the box take
+ * the Maxwellian of the face's boundary state (kin_set_boundary); axis
+ * velocity sets only.  The paper prescribes the solution on the boundary
+ * (Sec. 6.2) and upwinds with the value across every face (eq. dg_imp). */
 typedef struct {
     int dim;
     int n[3];
     double lo[3];
     double hi[3];
+    int inflow[3];
 } kin_mesh;
 
 /* Kinetic model.  lambda: kinetic speed |V_k| (must satisfy the
@@ -168,13 +173,23 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
  * m * nodes (else KIN_EINVAL).  Resets the step counter. */
 kin_status kin_set_state(kin_ctx* ctx, const double* W, size_t n_values, int on_device);
 
+/* Boundary state of face (axis, side) of an inflow axis (side 0: x_a = lo,
+ * side 1: x_a = hi): W holds m doubles (host memory, read before return).
+ * The populations entering the box through that face take M_k(W) there in
+ * every step and every subdomain iteration (the value is data, constant in
+ * time).  Every face of an inflow axis needs a state before the first step
+ * (else kin_step returns KIN_ESTATE).  KIN_EINVAL: axis not an inflow axis,
+ * side not 0 or 1, m wrong, or an Euler state with rho <= 0. */
+kin_status kin_set_boundary(kin_ctx* ctx, int axis, int side, const double* W, size_t m);
+
 /* Set the kinetic state f directly (checkpoint resume: after the first step
  * f != M(W), Sec. 2.2 remark, so W alone cannot restart a run).  f holds
  * npop * nodes values of the context precision. */
 kin_status kin_set_kinetic(kin_ctx* ctx, const void* f, size_t n_values, int on_device);
 
 /* Enqueue nsteps applications of S(dt) on the context stream and return
- * (asynchronous).  nsteps < 0: KIN_EINVAL; no state set: KIN_ESTATE. */
+ * (asynchronous).  nsteps < 0: KIN_EINVAL; no state set, or an inflow face
+ * without a boundary state: KIN_ESTATE. */
 kin_status kin_step(kin_ctx* ctx, int nsteps);
 
 /* W = sum_k f_k (Sec. 2.2, step 3) into W (m * nodes doubles).  Host
@@ -192,7 +207,8 @@ kin_status kin_get_kinetic(kin_ctx* ctx, void* f, size_t n_values, int on_device
  * times the face integral of (trace^{K-1} - trace^{K}) summed over every
  * upwind subdomain boundary (zero up to round-off when the iteration has
  * converged).  iter_residual (may be NULL): max over those faces of
- * |trace^{K} - trace^{K-1}|. */
+ * |trace^{K} - trace^{K-1}|.  With inflow axes only mass_per_var is
+ * available (next_defect or iter_residual: KIN_EINVAL). */
 kin_status kin_diag(kin_ctx* ctx, double* mass_per_var, double* next_defect, double* iter_residual);
 
 /* kin_step_noalloc -- nsteps steps of S(dt) without any device allocation.
@@ -202,8 +218,9 @@ kin_status kin_diag(kin_ctx* ctx, double* mass_per_var, double* next_defect, dou
  * fixed memory plan where an allocation failure at run time is not
  * acceptable.
  *
- * mesh, model, degree, dt: as kin_create.  opts: tiles, iters, precision,
- * block and stream are used; mem_budget and the allocator hooks are ignored.
+ * mesh, model, degree, dt: as kin_create (periodic axes only: a mesh with an
+ * inflow axis is KIN_EINVAL).  opts: tiles, iters, precision, block and
+ * stream are used; mem_budget and the allocator hooks are ignored.
  * f: device pointer to the caller's kinetic state, npop * nodes values of
  * opts->precision in the storage order above; read as f^n and overwritten
  * in place with f^{n + nsteps} (the caller owns it).  errbuf/errlen: optional
@@ -239,8 +256,10 @@ kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int de
  * default stream cannot hold the captured graphs); work already queued on a
  * member's stream runs before the batch step, and later work on it after.
  * Stepping a member alone while it is in a batch invalidates the batch
- * (KIN_ESTATE on the next kin_batch_step).  Errors: KIN_EINVAL (bad
- * arguments), KIN_ESTATE (member without state / poisoned / stepped alone),
+ * (KIN_ESTATE on the next kin_batch_step).  The batch takes its members'
+ * boundary states (kin_set_boundary) at creation.  Errors: KIN_EINVAL (bad
+ * arguments), KIN_ESTATE (member without state or without a boundary state
+ * on an inflow face / poisoned / stepped alone),
  * KIN_ECUDA, KIN_ENOMEM; messages from kin_batch_last_error. */
 typedef struct kin_batch kin_batch;
 kin_status kin_batch_create(kin_ctx* const* members, int count, void* stream, kin_batch** out);

@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
 EXPORTED = ["kin_create", "kin_set_state", "kin_set_kinetic", "kin_step", "kin_get_state",
             "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error",
             "kin_step_noalloc", "kin_batch_create", "kin_batch_create_ex", "kin_batch_step", "kin_batch_sync",
-            "kin_batch_destroy", "kin_batch_last_error"]
+            "kin_batch_destroy", "kin_batch_last_error", "kin_set_boundary"]
 
 
 class KinError(RuntimeError):
@@ -44,7 +44,7 @@ class KinError(RuntimeError):
 
 class kin_mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
-                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("inflow", ctypes.c_int * 3)]
 
 
 class kin_model(ctypes.Structure):
@@ -95,6 +95,7 @@ def load_library():
                                ctypes.c_double, ctypes.POINTER(kin_opts), ctypes.POINTER(vp)]
     lib.kin_set_state.argtypes = [vp, vp, sz, ctypes.c_int]
     lib.kin_set_kinetic.argtypes = [vp, vp, sz, ctypes.c_int]
+    lib.kin_set_boundary.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, sz]
     lib.kin_step.argtypes = [vp, ctypes.c_int]
     lib.kin_get_state.argtypes = [vp, vp, sz, ctypes.c_int]
     lib.kin_get_kinetic.argtypes = [vp, vp, sz, ctypes.c_int]
@@ -179,6 +180,12 @@ def kin_set_state(ctx, W, n_values=None):
     _check(ctx, load_library().kin_set_state(ctx, p, n if n_values is None else n_values, dev))
 
 
+def kin_set_boundary(ctx, axis, side, W):
+    W = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(-1))
+    _check(ctx, load_library().kin_set_boundary(ctx, int(axis), int(side),
+                                                W.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), W.size))
+
+
 def kin_set_kinetic(ctx, f, n_values=None):
     p, dev = _ptr(f)
     n = f.size if isinstance(f, np.ndarray) else f.numel()
@@ -201,14 +208,18 @@ def kin_get_kinetic(ctx, f, n_values=None):
     _check(ctx, load_library().kin_get_kinetic(ctx, p, n if n_values is None else n_values, dev))
 
 
-def kin_diag(ctx, m: int):
+def kin_diag(ctx, m: int, defect: bool = True):
+    """(mass per variable, next-step interface defect, iteration residual);
+    defect=False asks for the mass only (the defect and residual are None)."""
     mass = np.zeros(m)
-    defect = np.zeros(m)
+    dfc = np.zeros(m)
     resid = np.zeros(1)
     dp = ctypes.POINTER(ctypes.c_double)
-    _check(ctx, load_library().kin_diag(ctx, mass.ctypes.data_as(dp), defect.ctypes.data_as(dp),
-                                        resid.ctypes.data_as(dp)))
-    return mass, defect, float(resid[0])
+    null = ctypes.POINTER(ctypes.c_double)()
+    _check(ctx, load_library().kin_diag(ctx, mass.ctypes.data_as(dp),
+                                        dfc.ctypes.data_as(dp) if defect else null,
+                                        resid.ctypes.data_as(dp) if defect else null))
+    return (mass, dfc, float(resid[0])) if defect else (mass, None, None)
 
 
 def kin_sync(ctx):
@@ -295,10 +306,10 @@ def kin_last_error(ctx=None) -> str:
 def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 0.0),
               tiles=(1, 1, 1), iters=3, precision=KIN_FP64, block=(0, 0, 0), mem_budget=0,
               stream=None, torch_alloc=False, wait_timeout_s=0.0, debug_flags=0, threads=0, stages=0,
-              velset=None, sigma=0.0):
+              velset=None, sigma=0.0, inflow=(0, 0, 0)):
     pad = lambda t, fill: tuple(t) + (fill,) * (3 - len(tuple(t)))
     mesh = kin_mesh(dim, (ctypes.c_int * 3)(*pad(n, 1)), (ctypes.c_double * 3)(*pad(lo, 0.0)),
-                    (ctypes.c_double * 3)(*pad(hi, 1.0)))
+                    (ctypes.c_double * 3)(*pad(hi, 1.0)), (ctypes.c_int * 3)(*pad(inflow, 0)))
     model = kin_model(system, dim if velset is None else velset, lam, gamma,
                       (ctypes.c_double * 3)(*pad(adv, 0.0)), omega, sigma)
     opts = kin_opts()
@@ -364,9 +375,17 @@ class Context:
     def from_workload(cls, w, precision=None, **kw):
         prec = precision if precision is not None else (KIN_FP32 if w.precision == "f32" else KIN_FP64)
         vs = {2: KIN_D2Q3, 3: KIN_D3Q4}.get(w.dim) if getattr(w, "velset", 0) == 1 else None
-        return cls(w.dim, w.n, w.lo, w.hi, w.degree, w.system, w.lam, w.dt, omega=w.omega,
-                   gamma=w.gamma, adv=w.adv, tiles=w.tiles, iters=w.iters, precision=prec, velset=vs,
-                   sigma=getattr(w, "sigma", 0.0), **kw)
+        inflow = tuple(getattr(w, "inflow", (0, 0, 0)))
+        ctx = cls(w.dim, w.n, w.lo, w.hi, w.degree, w.system, w.lam, w.dt, omega=w.omega,
+                  gamma=w.gamma, adv=w.adv, tiles=w.tiles, iters=w.iters, precision=prec, velset=vs,
+                  sigma=getattr(w, "sigma", 0.0), inflow=inflow, **kw)
+        if any(inflow):
+            Wb = np.asarray(w.Wb, dtype=np.float64)
+            for a in range(w.dim):
+                if inflow[a]:
+                    for side in (0, 1):
+                        ctx.set_boundary(a, side, Wb[a, side, :w.m])
+        return ctx
 
     @property
     def dtype(self):
@@ -377,6 +396,9 @@ class Context:
 
     def set_kinetic(self, f):
         kin_set_kinetic(self.ctx, f)
+
+    def set_boundary(self, axis, side, W):
+        kin_set_boundary(self.ctx, axis, side, W)
 
     def step(self, n=1):
         kin_step(self.ctx, n)

@@ -23,6 +23,11 @@ struct kin_ctx {
     int dim = 1, n[3] = {1, 1, 1}, degree = 1, system = 0, m = 1, nvel = 2, npop = 2, NP = 2, NN = 2;
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1}, h[3] = {1, 1, 1};
     double lambda = 1, gamma = 1.4, adv[3] = {0, 0, 0}, omega = 2, dt = 0, sigma = 0;
+    // inflow boundaries: per axis flag, the value across the boundary face
+    // each population enters through, and which faces have a state
+    int inflow[3] = {0, 0, 0};
+    double bnd[kMaxPop] = {};
+    bool bnd_set[3][2] = {{false, false}, {false, false}, {false, false}};
     int tiles[3] = {1, 1, 1}, L[3] = {1, 1, 1}, iters = 3, precision = KIN_FP64;
     int B[3] = {1, 1, 1}, nblk[3] = {1, 1, 1}, nb[3] = {1, 1, 1};
     size_t cells = 0, nodes = 0, sig_stride = 0, raw_stride = 0, esize = 8;
@@ -246,6 +251,11 @@ static Inst make_inst(const kin_ctx* c, int mode)
     I.gamma = c->gamma;
     I.omega = c->omega;
     I.mu = c->system == KIN_MAXWELL ? (1.0 - 0.5 * c->sigma * c->dt) / (1.0 + 0.5 * c->sigma * c->dt) : 1.0;
+    for (int a = 0; a < 3; ++a) I.inflow[a] = c->inflow[a];
+    for (int p = 0; p < kMaxPop; ++p) {
+        I.bnd64[p] = c->bnd[p];
+        I.bnd32[p] = (float)c->bnd[p];
+    }
     return I;
 }
 
@@ -459,6 +469,12 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
         return fail(nullptr, KIN_EINVAL, "the conductivity sigma must be >= 0");
     const bool simplex = (model->velset == KIN_D2Q3 && mesh->dim == 2) ||
                          (model->velset == KIN_D3Q4 && mesh->dim == 3);
+    for (int a = 0; a < 3; ++a) {
+        if (mesh->inflow[a] != 0 && mesh->inflow[a] != 1)
+            return fail(nullptr, KIN_EINVAL, "inflow[%d] must be 0 or 1", a);
+        if (mesh->inflow[a] && (a >= mesh->dim || simplex))
+            return fail(nullptr, KIN_EINVAL, "inflow boundaries need an axis < dim and an axis velocity set");
+    }
     if (model->velset != mesh->dim && !simplex)
         return fail(nullptr, KIN_EINVAL, "velocity set %d does not match dim %d", model->velset, mesh->dim);
     if (simplex && (degree > (mesh->dim == 3 ? 2 : 3)))
@@ -486,6 +502,7 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     c->system = model->system;
     c->m = model->system == KIN_MAXWELL ? 6 : (model->system == KIN_EULER ? mesh->dim + 2 : 1);
     c->sigma = model->sigma;
+    for (int a = 0; a < 3; ++a) c->inflow[a] = mesh->inflow[a];
     c->simplex = simplex;
     c->nvel = simplex ? mesh->dim + 1 : 2 * mesh->dim;
     c->npop = c->nvel * c->m;
@@ -793,12 +810,45 @@ kin_status kin_set_kinetic(kin_ctx* c, const void* f, size_t n_values, int on_de
     return KIN_OK;
 }
 
+// An inflow face without a boundary state (name of the first one, or null).
+static const char* missing_boundary(const kin_ctx* c)
+{
+    static const char* names[3][2] = {{"x lower", "x upper"}, {"y lower", "y upper"}, {"z lower", "z upper"}};
+    for (int a = 0; a < 3; ++a)
+        for (int sd = 0; sd < 2; ++sd)
+            if (c->inflow[a] && !c->bnd_set[a][sd]) return names[a][sd];
+    return nullptr;
+}
+
+kin_status kin_set_boundary(kin_ctx* c, int axis, int side, const double* W, size_t m)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (axis < 0 || axis >= c->dim || !c->inflow[axis])
+        return fail(c, KIN_EINVAL, "axis %d is not an inflow axis", axis);
+    if (side != 0 && side != 1) return fail(c, KIN_EINVAL, "side must be 0 (lower) or 1 (upper)");
+    if (!W || m != (size_t)c->m) return fail(c, KIN_EINVAL, "expected %d boundary values", c->m);
+    for (int v = 0; v < c->m; ++v)
+        if (!std::isfinite(W[v])) return fail(c, KIN_EINVAL, "boundary state is not finite");
+    if (c->system == KIN_EULER && !(W[0] > 0.0)) return fail(c, KIN_EINVAL, "boundary density must be > 0");
+    double M[kMaxPop];
+    axis_maxwellian(point_args(c), W, M);
+    // the populations moving along +e_axis enter through the lower face, the
+    // ones moving along -e_axis through the upper face
+    const int k = 2 * axis + side;
+    for (int v = 0; v < c->m; ++v) c->bnd[k * c->m + v] = M[k * c->m + v];
+    c->bnd_set[axis][side] = true;
+    return KIN_OK;
+}
+
 kin_status kin_step(kin_ctx* c, int nsteps)
 {
     kin_status st = check_usable(c);
     if (st) return st;
     if (nsteps < 0) return fail(c, KIN_EINVAL, "nsteps must be >= 0");
     if (!c->have_state) return fail(c, KIN_ESTATE, "no state: call kin_set_state or kin_set_kinetic first");
+    if (const char* face = missing_boundary(c))
+        return fail(c, KIN_ESTATE, "the %s face of an inflow axis has no boundary state (kin_set_boundary)", face);
     for (int s = 0; s < nsteps; ++s) {
         st = c->simplex ? sx_step(c) : launch_step(c, 0);
         if (st) return st;
@@ -848,6 +898,8 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
     kin_status st = check_usable(c);
     if (st) return st;
     if (!c->have_state) return fail(c, KIN_ESTATE, "no state has been set");
+    if ((next_defect || iter_residual) && (c->inflow[0] || c->inflow[1] || c->inflow[2]))
+        return fail(c, KIN_EINVAL, "next_defect and iter_residual are not available with inflow axes");
     double host[8] = {0};
     if (mass_per_var) {
         KIN_CUDA(c, launch_mass(point_args(c), c->f, c->gll, c->partial, c->result,
@@ -1067,6 +1119,8 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
         if (!members[i]) return batch_fail(nullptr, KIN_EINVAL, "member %d is NULL", i);
         if (members[i]->poisoned) return batch_fail(nullptr, KIN_ESTATE, "member %d is poisoned", i);
         if (!members[i]->have_state) return batch_fail(nullptr, KIN_ESTATE, "member %d has no state", i);
+        if (missing_boundary(members[i]))
+            return batch_fail(nullptr, KIN_ESTATE, "member %d has an inflow face without a boundary state", i);
         if (members[i]->simplex)
             return batch_fail(nullptr, KIN_EINVAL, "member %d uses a d+1 velocity set (not batched)", i);
         for (int j = 0; j < i; ++j)
@@ -1185,6 +1239,8 @@ extern "C" kin_status kin_batch_step(kin_batch* b, int nsteps)
         if (c->poisoned) return batch_fail(b, KIN_ESTATE, "member %zu is poisoned", i);
         if (c->cur != (b->expect_cur[i] ^ b->parity))
             return batch_fail(b, KIN_ESTATE, "member %zu was stepped outside the batch", i);
+        if (missing_boundary(c))
+            return batch_fail(b, KIN_ESTATE, "member %zu has an inflow face without a boundary state", i);
     }
     if (nsteps == 0) return KIN_OK;
     cudaError_t e = cudaSuccess;
@@ -1305,6 +1361,7 @@ extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* mo
     if (mesh->dim < 1 || mesh->dim > 3 || degree < 1 || degree > 3 ||
         (model->system != KIN_ADVECTION && model->system != KIN_EULER && model->system != KIN_MAXWELL) ||
         (model->system == KIN_MAXWELL && (mesh->dim != 3 || !(model->sigma >= 0.0))) || model->velset != mesh->dim ||
+        mesh->inflow[0] || mesh->inflow[1] || mesh->inflow[2] ||
         !(model->lambda > 0) || !(dt > 0) || !(model->omega >= 1.0 && model->omega <= 2.0) ||
         (model->system == KIN_EULER && !(model->gamma > 1.0)) || opts->iters < 1 ||
         (opts->precision != KIN_FP64 && opts->precision != KIN_FP32)) {

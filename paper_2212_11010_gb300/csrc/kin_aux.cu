@@ -150,7 +150,7 @@ __global__ void setup_kernel(SetupArgs A)
 
 // Flux in FP64 (eq. conslaw): scalar advection, Euler, or Maxwell in 3D
 // (Sec. 6.1.1: Q(W, e_a) = (-e_a x H, e_a x E), W = (E, H)).
-__device__ static void flux64(const PointArgs& A, const double* W, int a, double* Q)
+__host__ __device__ static void flux64(const PointArgs& A, const double* W, int a, double* Q)
 {
     if (A.system == kAdvection) {
         Q[0] = A.adv[a] * W[0];
@@ -175,6 +175,21 @@ __device__ static void flux64(const PointArgs& A, const double* W, int a, double
     Q[0] = W[1 + a];
     for (int b = 0; b < d; ++b) Q[1 + b] = W[1 + b] * ua + (b == a ? pr : 0.0);
     Q[1 + d] = (E + pr) * ua;
+}
+
+// The 2d-velocity Maxwellians of one state on the host, in FP64, with the
+// formulas of init_kernel: M[(2a + s) m + v] = W_v/(2d) +- Q^a(W)_v/(2 lambda).
+void axis_maxwellian(const PointArgs& A, const double* W, double* M)
+{
+    double Q[kMaxVars];
+    for (int a = 0; a < A.dim; ++a) {
+        flux64(A, W, a, Q);
+        for (int v = 0; v < A.m; ++v) {
+            const double base = W[v] / (2.0 * A.dim), half = Q[v] / (2.0 * A.lambda);
+            M[(2 * a) * A.m + v] = base + half;
+            M[(2 * a + 1) * A.m + v] = base - half;
+        }
+    }
 }
 
 // f = M(W) (Sec. 2.2 initialisation), W in FP64, f stored in T.

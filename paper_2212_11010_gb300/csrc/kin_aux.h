@@ -85,6 +85,8 @@ cudaError_t sx_launch_init(const SxArgs& a, const double* W, int prec, cudaStrea
 
 cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st);
 cudaError_t launch_init(const PointArgs& a, const double* W, void* f, int prec, cudaStream_t st);
+// host: the 2d-velocity Maxwellians M[(2a + s) m + v] of one state (FP64)
+void axis_maxwellian(const PointArgs& a, const double* W, double* M);
 cudaError_t launch_moments(const PointArgs& a, const void* f, double* W, int prec, cudaStream_t st);
 cudaError_t launch_mass(const PointArgs& a, const void* f, const double* gll, double* partial,
                         double* out, int prec, cudaStream_t st);

@@ -49,6 +49,7 @@ constexpr int kMaxwell = 2;        // 3D only: W = (E, H) (Sec. 6.1.1)
 // conserved variables m of a system in D dimensions
 __host__ __device__ constexpr int nvars(int D, int SYS) { return SYS == kAdvection ? 1 : (SYS == kMaxwell ? 6 : D + 2); }
 constexpr int kCoefStride = 32;    // coefficient slots per (axis, sign)
+constexpr int kMaxPop = 36;        // populations at most (axis velocities: 2d x m, Maxwell 6 x 6)
 constexpr int kThreads = 256;      // upper bound on threads per block
 
 // coefficient slot layout inside one (axis, sign) record
@@ -101,6 +102,11 @@ struct __align__(16) Inst {
     int debug_stall;         // test hook: the load barrier expects 16 bytes that never arrive
     double lambda, gamma, omega;
     double mu;               // Maxwell: conductivity source factor (1 - sigma dt/2) / (1 + sigma dt/2)
+    int inflow[3];           // 1: axis a has inflow boundaries instead of being periodic
+    // inflow boundaries: the value across the domain-boundary face that
+    // population pop enters through, M_k(W_b)[v] of that face's state
+    double bnd64[kMaxPop];
+    float bnd32[kMaxPop];
     double adv[3];
     // block-inverse coefficients (computed in FP64 on the device once per
     // context), carried in the launch parameters: read from the constant bank
@@ -127,6 +133,13 @@ __device__ __forceinline__ double coef_of(const Inst& I, int dir, int k, double)
 // Summaries are stored [block q (downwind order)][line], raw values
 // [subdomain][line]; every load is coalesced across consecutive lines.
 template <typename T>
+__device__ __forceinline__ T bnd_of(const Inst& I, int pop);
+template <>
+__device__ __forceinline__ float bnd_of<float>(const Inst& I, int pop) { return I.bnd32[pop]; }
+template <>
+__device__ __forceinline__ double bnd_of<double>(const Inst& I, int pop) { return I.bnd64[pop]; }
+
+template <typename T>
 __device__ __forceinline__ T chain_inflow(const Inst& I, int a, int sgn, int bidx, int pop, long long gline)
 {
     const int nbk = I.nblk[a], nb = I.nb[a], NS = I.NS[a], K = I.iters;
@@ -137,11 +150,23 @@ __device__ __forceinline__ T chain_inflow(const Inst& I, int a, int sgn, int bid
     const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)pop * I.raw_stride + gline;
     const T RB = coef_of(I, 2 * a + sgn, kOffRhoB, T(0));
     int s0 = S - K;
-    while (s0 < 0) s0 += NS;
-    T t = __ldg(raw + (long long)s0 * gl);
-    const int cnt = (K - 1) * nb + r;
+    T t;
+    int cnt;
+    const T* p;
+    if (I.inflow[a] && s0 < 0) {
+        // the walk reaches the domain boundary within K subdomains: it starts
+        // there from the boundary value (the same in every iteration) and
+        // folds every block from the first one
+        t = bnd_of<T>(I, pop);
+        cnt = S * nb + r;
+        p = sig;
+    } else {
+        while (s0 < 0) s0 += NS;
+        t = __ldg(raw + (long long)s0 * gl);
+        cnt = (K - 1) * nb + r;
+        p = sig + (long long)((s0 + 1 == NS) ? 0 : (s0 + 1) * nb) * gl;
+    }
     // walk the summaries of blocks q0, q0+1, ... (periodic) by pointer stride
-    const T* p = sig + (long long)((s0 + 1 == NS) ? 0 : (s0 + 1) * nb) * gl;
     const T* const end = sig + (long long)nbk * gl;
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {

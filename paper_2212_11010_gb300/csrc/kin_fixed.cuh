@@ -451,10 +451,13 @@ __device__ __forceinline__ void chain_setup(const Inst& I, int hid, int sgn, int
     const int Sd = (int)fdiv((unsigned)q, I.fd_nb[A]);
     const int r = q - Sd * nbs;
     int s0 = Sd - K;
+    // an inflow axis whose walk reaches the domain boundary starts there from
+    // the boundary value and folds every block from the first one
+    const bool from_bnd = I.inflow[A] && s0 < 0;
     while (s0 < 0) s0 += NSa;
     const long long gl = I.ax[A].glines;
-    cnt = (K - 1) * nbs + r;
-    qj = (s0 + 1 == NSa) ? 0 : (s0 + 1) * nbs;
+    cnt = from_bnd ? Sd * nbs + r : (K - 1) * nbs + r;
+    qj = from_bnd ? 0 : ((s0 + 1 == NSa) ? 0 : (s0 + 1) * nbs);
     RB = coef_of(I, 2 * A + sgn, kOffRhoB, T(0));
     const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)s0 * gl;
 #pragma unroll
@@ -469,7 +472,7 @@ __device__ __forceinline__ void chain_setup(const Inst& I, int hid, int sgn, int
         const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
         const int pop = (2 * A + sgn) * M + v;
         off[k] = (int)((long long)pop * I.sig_stride + gline);   // fits: checked on the host
-        tr[k] = __ldg(raw + (long long)pop * I.raw_stride + gline);
+        tr[k] = from_bnd ? bnd_of<T>(I, pop) : __ldg(raw + (long long)pop * I.raw_stride + gline);
     }
 }
 

@@ -40,7 +40,8 @@ def test_library_exports_every_declared_symbol(kin):
 BAD = [
     dict(dim=4), dict(degree=0), dict(degree=4), dict(system=7), dict(lam=-1.0), dict(dt=0.0),
     dict(omega=2.5), dict(omega=0.5), dict(iters=0), dict(precision=9), dict(tiles=(3, 1)),
-    dict(block=(3, 1)), dict(velset=1), dict(gamma=1.0), dict(system=2),
+    dict(block=(3, 1)), dict(velset=1), dict(gamma=1.0), dict(system=2), dict(inflow=(2, 0)),
+    dict(inflow=(0, 0, 1)), dict(inflow=(1, 0), velset=4),
 ]
 
 

@@ -73,6 +73,8 @@ class Workload:
     exact: Optional[Callable] = field(default=None, repr=False)  # exact(t) -> W
     velset: int = 0           # 0: 2d velocities +-lambda e_a; 1: d + 1 velocities (D2Q3, D3Q4)
     sigma: float = 0.0        # conductivity (Maxwell only)
+    inflow: tuple = (0, 0, 0)  # 1: axis a has inflow boundaries instead of being periodic
+    Wb: object = field(default=None, repr=False)   # boundary states (3 axes, 2 faces, m)
 
     @property
     def m(self) -> int:
@@ -98,7 +100,7 @@ class Workload:
         return dict(dim=self.dim, n=self.n, lo=self.lo, hi=self.hi, degree=self.degree,
                     system=self.system, lam=self.lam, dt=self.dt, omega=self.omega,
                     gamma=self.gamma, adv=self.adv, tiles=self.tiles, iters=self.iters,
-                    velset=self.velset, sigma=self.sigma)
+                    velset=self.velset, sigma=self.sigma, inflow=self.inflow, Wb=self.Wb)
 
 
 def node_coords(dim, n, lo, hi, degree) -> np.ndarray:
