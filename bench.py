@@ -91,6 +91,12 @@ def make_workload(name):
     elif name == "vortex2d-512-p3":
         w = workloads.with_(workloads.vortex2d(seed=0, n=512, degree=3), tiles=(16, 16))
         desc = "vortex2d-euler-512x512-p3-D2Q4-16x16sub-K3"
+    elif name == "maxwell3d-dirichlet":
+        # every face a domain boundary with the homogeneous Dirichlet state
+        # (zero field), as in the paper's body-model run
+        w = workloads.with_(workloads.maxwell3d(seed=0, n=128, degree=1, tiles=16, sigma=1.0),
+                            inflow=(1, 1, 1), Wb=np.zeros((3, 2, 6)))
+        desc = "maxwell3d-128^3-p1-D3Q6-16^3sub-K3-sigma1-dirichlet0"
     elif name == "maxwell3d":
         w = workloads.maxwell3d(seed=0, n=128, degree=1, tiles=16, sigma=1.0)
         desc = "maxwell3d-128^3-p1-D3Q6-16^3sub-K3-sigma1"
@@ -551,7 +557,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="vortex2d",
                     choices=["vortex2d", "densitywave3d", "advection1d", "batched", "serving",
-                             "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d", "vortex2d-512-p3"])
+                             "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d", "vortex2d-512-p3",
+                             "maxwell3d-dirichlet"])
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
