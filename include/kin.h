@@ -176,9 +176,12 @@ kin_status kin_set_state(kin_ctx* ctx, const double* W, size_t n_values, int on_
 /* Boundary state of face (axis, side) of an inflow axis (side 0: x_a = lo,
  * side 1: x_a = hi): W holds m doubles (host memory, read before return).
  * The populations entering the box through that face take M_k(W) there in
- * every step and every subdomain iteration (the value is data, constant in
- * time).  Every face of an inflow axis needs a state before the first step
- * (else kin_step returns KIN_ESTATE).  KIN_EINVAL: axis not an inflow axis,
+ * every step and every subdomain iteration (the value is data) until the
+ * next call.  Time-dependent boundary data: set the state at the step's
+ * midpoint t^n + dt/2 before each kin_step(ctx, 1) (the implicit half step of
+ * Crank-Nicolson sits there; data at t^n or t^{n+1} lose an order).  Every
+ * face of an inflow axis needs a state before the first step (else kin_step
+ * returns KIN_ESTATE).  KIN_EINVAL: axis not an inflow axis,
  * side not 0 or 1, m wrong, or an Euler state with rho <= 0. */
 kin_status kin_set_boundary(kin_ctx* ctx, int axis, int side, const double* W, size_t m);
 

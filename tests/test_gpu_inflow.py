@@ -130,3 +130,45 @@ def test_batch_with_inflow_members_equals_alone(kin):
     finally:
         for c in ctxs:
             c.close()
+
+
+def _plane_wave(x, t):
+    # E_z = cos(2 pi (x - t)), H_y = -E_z: a wave moving along +x (Sec. 6.2 form)
+    W = np.zeros((6,) + np.shape(x))
+    W[2] = np.cos(2 * np.pi * (x - t))
+    W[4] = -W[2]
+    return W
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", TOL64), ("f32", TOL32)])
+def test_plane_wave_with_exact_dirichlet_data_matches_oracle(kin, precision, tol):
+    # non-periodic x with the exact solution imposed on both x faces at every
+    # step's midpoint (boundary states set before each step), periodic y, z
+    import oracle
+    w = workloads.maxwell3d(seed=6, n=8, degree=2, tiles=2, dt_mult=3.0, precision=precision)
+    w = workloads.with_(w, n=(16, 2, 2), tiles=(4, 1, 1), inflow=(1, 0, 0), Wb=np.zeros((3, 2, 6)))
+    P = oracle.Problem(**w.oracle_kwargs())
+    x = oracle.node_coords(P)[:, 0]
+    W0 = _plane_wave(x, 0.0)
+    steps = 6
+    pr = kin.KIN_FP64 if precision == "f64" else kin.KIN_FP32
+    with kin.Context.from_workload(workloads.with_(w, W0=W0), precision=pr) as ctx:
+        ctx.set_state(np.ascontiguousarray(W0.reshape(-1)))
+        fo = oracle.init(P, W0)
+        for s in range(steps):
+            tm = (s + 0.5) * w.dt
+            wb = np.zeros((3, 2, 6))
+            wb[0, 0], wb[0, 1] = _plane_wave(0.0, tm), _plane_wave(1.0, tm)
+            ctx.set_boundary(0, 0, wb[0, 0])
+            ctx.set_boundary(0, 1, wb[0, 1])
+            ctx.step(1)
+            P.Wb = wb
+            oracle.step(P, fo, 1)
+        W = ctx.get_state()
+    Wo = oracle.moments(P, fo)
+    # E_x, E_y, H_x, H_z stay zero up to round-off, so the error is taken
+    # relative to the largest field value rather than per variable
+    err = np.abs(W - Wo).max() / np.abs(Wo).max()
+    assert err < tol, err
+    # and the result is the travelling wave (the scheme's error, not round-off)
+    assert np.abs(W.reshape(6, -1) - _plane_wave(x, steps * w.dt)).max() < 0.1

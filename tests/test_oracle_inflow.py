@@ -153,3 +153,33 @@ def test_bump_with_inflow_converges_to_translation_at_second_order():
         errs.append(np.abs(u - _bump(x - T)).max())
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert errs[-1] < 3e-3 and rates.min() > 1.85, (errs, rates)
+
+
+def _advect_with_boundary_data(n, when, T=0.25):
+    # u_t + u_x = 0 on [0, 1], u = sin(2 pi (x - t)) + 2 exactly; the boundary
+    # states of both faces are set from the exact solution before every step,
+    # at time t^n + when * dt
+    steps = n // 4
+    dt = T / steps
+    P = oracle.Problem(dim=1, n=(n,), lo=(0.0,), hi=(1.0,), degree=2, system=oracle.ADVECTION, lam=1.5,
+                       dt=dt, adv=(1.0, 0, 0), tiles=(4,), iters=3, inflow=(1,), Wb=np.zeros((3, 2, 1)))
+    x = oracle.node_coords(P)[:, 0]
+    exact = lambda x, t: np.sin(2 * np.pi * (x - t)) + 2.0
+    f = oracle.init(P, exact(x, 0.0)[None, :])
+    for s in range(steps):
+        t = (s + when) * dt
+        wb = np.zeros((3, 2, 1))
+        wb[0, 0, 0], wb[0, 1, 0] = exact(0.0, t), exact(1.0, t)
+        P.Wb = wb
+        oracle.step(P, f, 1)
+    return np.abs(oracle.moments(P, f).reshape(-1) - exact(x, T)).max()
+
+
+def test_time_dependent_boundary_data_enter_at_the_midpoint():
+    # the implicit half step of Crank-Nicolson sits at t^{n+1/2}: boundary
+    # data taken there keep second order, data at t^n or t^{n+1} drop to first
+    def order(when):
+        e = [_advect_with_boundary_data(n, when) for n in (64, 128, 256)]
+        return np.log2(e[0] / e[1]), np.log2(e[1] / e[2])
+    assert min(order(0.5)) > 1.9
+    assert max(order(0.0)) < 1.2 and max(order(1.0)) < 1.2
