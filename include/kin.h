@@ -259,8 +259,8 @@ kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int de
  * default stream cannot hold the captured graphs); work already queued on a
  * member's stream runs before the batch step, and later work on it after.
  * Stepping a member alone while it is in a batch invalidates the batch
- * (KIN_ESTATE on the next kin_batch_step).  The batch takes its members'
- * boundary states (kin_set_boundary) at creation.  Errors: KIN_EINVAL (bad
+ * (KIN_ESTATE on the next kin_batch_step).  A member's kin_set_boundary
+ * applies from the next batch step on.  Errors: KIN_EINVAL (bad
  * arguments), KIN_ESTATE (member without state or without a boundary state
  * on an inflow face / poisoned / stepped alone),
  * KIN_ECUDA, KIN_ENOMEM; messages from kin_batch_last_error. */

@@ -27,6 +27,8 @@ struct kin_ctx {
     // each population enters through, and which faces have a state
     int inflow[3] = {0, 0, 0};
     double bnd[kMaxPop] = {};
+    double bnd_host[kMaxPop] = {};    // the values in the context precision, staged for the device copy
+    void* bnd_dev = nullptr;          // T[npop] on the device, read by the look-back
     bool bnd_set[3][2] = {{false, false}, {false, false}, {false, false}};
     int tiles[3] = {1, 1, 1}, L[3] = {1, 1, 1}, iters = 3, precision = KIN_FP64;
     int B[3] = {1, 1, 1}, nblk[3] = {1, 1, 1}, nb[3] = {1, 1, 1};
@@ -252,10 +254,7 @@ static Inst make_inst(const kin_ctx* c, int mode)
     I.omega = c->omega;
     I.mu = c->system == KIN_MAXWELL ? (1.0 - 0.5 * c->sigma * c->dt) / (1.0 + 0.5 * c->sigma * c->dt) : 1.0;
     for (int a = 0; a < 3; ++a) I.inflow[a] = c->inflow[a];
-    for (int p = 0; p < kMaxPop; ++p) {
-        I.bnd64[p] = c->bnd[p];
-        I.bnd32[p] = (float)c->bnd[p];
-    }
+    I.bnd = c->bnd_dev;
     return I;
 }
 
@@ -719,6 +718,7 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     ALLOC(c->partial, sizeof(double) * kDiagBlocks * (kMaxVars + 1));
     ALLOC(c->result, sizeof(double) * 8);
     ALLOC(c->errword, sizeof(int) * 4);
+    if (c->inflow[0] || c->inflow[1] || c->inflow[2]) ALLOC(c->bnd_dev, sizeof(double) * kMaxPop);
 #undef ALLOC
     if (c->esize == 8) c->coef = c->c64;
 
@@ -837,6 +837,15 @@ kin_status kin_set_boundary(kin_ctx* c, int axis, int side, const double* W, siz
     // ones moving along -e_axis through the upper face
     const int k = 2 * axis + side;
     for (int v = 0; v < c->m; ++v) c->bnd[k * c->m + v] = M[k * c->m + v];
+    // the device copy, in the context precision, stream-ordered before the next step
+    if (c->esize == 4) {
+        float* h = reinterpret_cast<float*>(c->bnd_host);
+        for (int p = 0; p < c->npop; ++p) h[p] = (float)c->bnd[p];
+    } else {
+        for (int p = 0; p < c->npop; ++p) c->bnd_host[p] = c->bnd[p];
+    }
+    KIN_CUDA(c, cudaMemcpyAsync(c->bnd_dev, c->bnd_host, (size_t)c->npop * c->esize, cudaMemcpyHostToDevice,
+                                c->stream));
     c->bnd_set[axis][side] = true;
     return KIN_OK;
 }

@@ -103,10 +103,9 @@ struct __align__(16) Inst {
     double lambda, gamma, omega;
     double mu;               // Maxwell: conductivity source factor (1 - sigma dt/2) / (1 + sigma dt/2)
     int inflow[3];           // 1: axis a has inflow boundaries instead of being periodic
-    // inflow boundaries: the value across the domain-boundary face that
-    // population pop enters through, M_k(W_b)[v] of that face's state
-    double bnd64[kMaxPop];
-    float bnd32[kMaxPop];
+    // T*: inflow boundaries: per population the value across the
+    // domain-boundary face it enters through, M_k(W_b)[v] of that face's state
+    const void* bnd;
     double adv[3];
     // block-inverse coefficients (computed in FP64 on the device once per
     // context), carried in the launch parameters: read from the constant bank
@@ -133,11 +132,10 @@ __device__ __forceinline__ double coef_of(const Inst& I, int dir, int k, double)
 // Summaries are stored [block q (downwind order)][line], raw values
 // [subdomain][line]; every load is coalesced across consecutive lines.
 template <typename T>
-__device__ __forceinline__ T bnd_of(const Inst& I, int pop);
-template <>
-__device__ __forceinline__ float bnd_of<float>(const Inst& I, int pop) { return I.bnd32[pop]; }
-template <>
-__device__ __forceinline__ double bnd_of<double>(const Inst& I, int pop) { return I.bnd64[pop]; }
+__device__ __forceinline__ T bnd_of(const Inst& I, int pop)
+{
+    return __ldg(static_cast<const T*>(I.bnd) + pop);
+}
 
 template <typename T>
 __device__ __forceinline__ T chain_inflow(const Inst& I, int a, int sgn, int bidx, int pop, long long gline)

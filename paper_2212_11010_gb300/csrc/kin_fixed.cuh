@@ -472,7 +472,7 @@ __device__ __forceinline__ void chain_setup(const Inst& I, int hid, int sgn, int
         const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
         const int pop = (2 * A + sgn) * M + v;
         off[k] = (int)((long long)pop * I.sig_stride + gline);   // fits: checked on the host
-        tr[k] = from_bnd ? bnd_of<T>(I, pop) : __ldg(raw + (long long)pop * I.raw_stride + gline);
+        tr[k] = __ldg(from_bnd ? static_cast<const T*>(I.bnd) + pop : raw + (long long)pop * I.raw_stride + gline);
     }
 }
 
