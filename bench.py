@@ -67,8 +67,8 @@ def flops_per_dof(dim, degree, m, nvel, maxwell=False):
 # kernel and workload (profiles/step_kernel_fixed_vortex2d_256x256_p2.md,
 # profiles/step_kernel_fixed_vortex2d_512x512_p3.md); stores still in L2 at
 # kernel end are not counted by the capture.
-NCU_TRAFFIC = {("vortex2d", "f32"): 39.759616e6 + 0.024e6,
-               ("vortex2d-512-p3", "f32"): 279.486976e6 + 220.965376e6}
+NCU_TRAFFIC = {("vortex2d", "f32"): 39.760384e6 + 0.0704e6,
+               ("vortex2d-512-p3", "f32"): 279.491328e6 + 217.914624e6}
 
 
 def make_workload(name):
