@@ -1,16 +1,19 @@
 // kin_fixed.cuh -- the fused step kernel for a compile-time cell-block shape.
 //
-// Same computation as the generic kernel of kin_device.cuh (bulk loads,
-// look-back inflow, downwind sweeps, relaxation, block summaries, bulk
-// stores), specialised on the block extents B0 x B1 x B2 and the thread count
-// NTH so that every loop has a constant trip count and every shared-memory
-// offset is an immediate.  Differences in the schedule:
+// Same computation as the generic kernel of kin_device.cuh (look-back
+// inflow, tile load, downwind sweeps, relaxation, tile store, block
+// summaries), specialised on the block extents B0 x B1 x B2 and the thread
+// count NTH so that every loop has a constant trip count and every
+// shared-memory offset is an immediate.  Differences in the schedule:
+//   * the look-back runs first, split over two thread halves (one per
+//     velocity sign), then the tile moves as 16-byte cp.async chunks from
+//     every thread; stores are 16-byte vector stores;
 //   * shared memory rows and population slabs are padded (by a multiple of 16
-//     bytes, which keeps bulk copies legal) with the padding that minimises
-//     bank conflicts of the sweep and relaxation access patterns, chosen at
-//     compile time;
-//   * the threads are split in two halves, one per velocity sign, so each
-//     warp sweeps lines of a single direction with no per-cell selects.
+//     bytes, which keeps the vector copies legal) with the padding that
+//     minimises bank conflicts of the sweep and relaxation access patterns,
+//     chosen at compile time (degree 3 in 2D: grouped sweeps, pm_group4);
+//   * a sweep item is one (axis, variable, line) for both velocity signs;
+//     the relaxation works on node pairs with packed FP32 instructions.
 #pragma once
 
 #include <type_traits>
