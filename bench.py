@@ -71,6 +71,24 @@ NCU_TRAFFIC = {("vortex2d", "f32"): 39.760384e6 + 0.0704e6,
                ("vortex2d-512-p3", "f32"): 279.491328e6 + 217.914624e6}
 
 
+def host_cpu():
+    """The host CPU the oracle baseline ran on: model (or part id on Arm
+    hosts without a model name) and the number of online cores."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    return {"model": model or platform.processor() or platform.machine(), "online_cores": os.cpu_count()}
+
+
 def make_workload(name):
     import workloads
     if name == "vortex2d":
@@ -256,7 +274,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": desc, "kinetic_dofs": w.kinetic_dofs, "parallelism": "cpu-1thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one full step of {sample}"},
+                         "sample": f"each step: one full step of {sample}", "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -399,7 +417,7 @@ def run_ours(args):
         if ws == 1 and not args.no_cpu_baseline:
             rate, nst, el = cpu_oracle_rate(w)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"{nst} full steps of {desc} in {el:.1f} s"}
+                                    "sample": f"{nst} full steps of {desc} in {el:.1f} s", "host": host_cpu()}
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
