@@ -89,6 +89,23 @@ def host_cpu():
     return {"model": model or platform.processor() or platform.machine(), "online_cores": os.cpu_count()}
 
 
+def replica_aggregate(local_ms, steps, units_per_rank, device="cuda"):
+    """Whole-job figures of N independent replicas: the slowest rank's timed
+    region (max over ranks, after a barrier) and the units all ranks
+    processed per second over it.  Single process: the local figures."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    max_ms = float(local_ms)
+    if ws > 1:
+        dist.barrier()
+        t = torch.tensor([float(local_ms)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    ms_per_step = max_ms / steps
+    return ms_per_step, ws * units_per_rank / (ms_per_step * 1e-3)
+
+
 def make_workload(name):
     import workloads
     if name == "vortex2d":
@@ -345,15 +362,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     times = [s.elapsed_time(e) for s, e in zip(starts, ends)]   # ms
     local_ms = float(np.sum(times))
-    if ws > 1:
-        dist.barrier()
-        t = torch.tensor([local_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_ms = float(t.item())
-    else:
-        max_ms = local_ms
-    ms_per_step = max_ms / args.steps
-    value = ws * dofs / (ms_per_step * 1e-3)
+    ms_per_step, value = replica_aggregate(local_ms, args.steps, dofs)
 
     # the same step through the public C ABI with host buffers: pinned host
     # f -> kin_set_kinetic -> kin_step(1) -> kin_get_kinetic -> pinned host
