@@ -32,7 +32,10 @@ SIMPLEX = 1     # d + 1 velocities (D1Q2, D2Q3, D3Q4)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, portable: x86_64 and aarch64).
+    """Compile the oracle with gcc (plain -O2, portable: x86_64 and aarch64),
+    with OpenMP when the compiler has it (the parallel loops run over the
+    subdomains of one iteration and over nodes; results do not depend on the
+    thread count).
 
     ``KIN_ORACLE_LIB`` names a prebuilt oracle library to load instead (used
     by the planted-mistake test, which builds altered copies of the source)."""
@@ -43,8 +46,11 @@ def build(force: bool = False) -> str:
         os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
     if force or stale:
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
-                               _SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)          # no OpenMP runtime: one thread
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -98,6 +104,7 @@ def lib():
             "ko_relax": ([pp, dp], ctypes.c_int),
             "ko_step": ([pp, dp, ctypes.c_int], ctypes.c_int),
             "ko_mass": ([pp, dp, dp], ctypes.c_int),
+            "ko_set_threads": ([ctypes.c_int], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(_lib, name)
@@ -266,3 +273,9 @@ def mass(P: Problem, W: np.ndarray) -> np.ndarray:
     out = np.zeros(P.m)
     _check(lib().ko_mass(ctypes.byref(P.c()), _dp(np.ascontiguousarray(W)), _dp(out)), "mass")
     return out
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops (n <= 0: unchanged); returns
+    the count in use (1 when built without OpenMP)."""
+    return int(lib().ko_set_threads(int(n)))

@@ -37,6 +37,14 @@
  *     data, the same in every subdomain iteration, and such faces are not
  *     interfaces (no mass defect).
  *
+ * Threads (OpenMP, when the library is built with it): within one
+ * subdomain iteration the subdomains are independent (every inflow across a
+ * subdomain boundary comes from the previous iterate), so the loop over
+ * subdomains runs in parallel -- the paper's own subdomain parallelism of
+ * Sec. 5.1 -- and the pointwise loops (initialisation, moments, relaxation)
+ * run in parallel over nodes.  Each cell's arithmetic is the same whatever
+ * the thread count, so results are bitwise independent of it.
+ *
  * parity pinned: see tests/test_oracle_*.py (closed forms, dense global
  * assembly, dense block-Jacobi assembly, conservation, exact solutions).
  */
@@ -46,6 +54,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -626,13 +637,14 @@ static int transport_population(const ko_problem* P, int k, int v, double* f, do
 
     int maxit = P->iters > 0 ? P->iters : 100000;
     int it;
+    const int nsub = P->tiles[0] * P->tiles[1] * P->tiles[2];
     for (it = 1; it <= maxit; ++it) {
-        for (int sz = 0; sz < P->tiles[2]; ++sz)
-            for (int sy = 0; sy < P->tiles[1]; ++sy)
-                for (int sx = 0; sx < P->tiles[0]; ++sx) {
-                    int s[3] = {sx, sy, sz};
-                    sweep_subdomain(&C, s, f, prev, cur);
-                }
+        /* the subdomains of one iteration are independent (eq. ibvp) */
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int si = 0; si < nsub; ++si) {
+            int s[3] = {si % P->tiles[0], (si / P->tiles[0]) % P->tiles[1], si / (P->tiles[0] * P->tiles[1])};
+            sweep_subdomain(&C, s, f, prev, cur);
+        }
         if (P->iters == 0) {
             double dmax = 0.0, fmax = 0.0;
             for (size_t i = 0; i < nodes; ++i) {
@@ -686,12 +698,14 @@ int ko_moments(const ko_problem* P, const double* f, double* W)
     if (check_problem(P) || !f || !W) return -1;
     int m = ko_num_vars(P), nv = ko_num_vel(P);
     size_t nodes = ko_num_nodes(P);
-    for (int v = 0; v < m; ++v)
+    for (int v = 0; v < m; ++v) {
+#pragma omp parallel for schedule(static)
         for (size_t i = 0; i < nodes; ++i) {
             double s = 0.0;
             for (int k = 0; k < nv; ++k) s += f[(size_t)(k * m + v) * nodes + i];
             W[(size_t)v * nodes + i] = s;
         }
+    }
     return 0;
 }
 
@@ -700,8 +714,9 @@ int ko_relax(const ko_problem* P, double* f)
     if (check_problem(P) || !f) return -1;
     int m = ko_num_vars(P), nv = ko_num_vel(P);
     size_t nodes = ko_num_nodes(P);
-    double W[8], M[64];
+#pragma omp parallel for schedule(static)
     for (size_t i = 0; i < nodes; ++i) {
+        double W[8], M[64];
         for (int v = 0; v < m; ++v) {
             double s = 0.0;
             for (int k = 0; k < nv; ++k) s += f[(size_t)(k * m + v) * nodes + i];
@@ -734,8 +749,9 @@ int ko_init(const ko_problem* P, const double* W0, double* f)
     if (check_problem(P) || !W0 || !f) return -1;
     int m = ko_num_vars(P), nv = ko_num_vel(P);
     size_t nodes = ko_num_nodes(P);
-    double W[8], M[64];
+#pragma omp parallel for schedule(static)
     for (size_t i = 0; i < nodes; ++i) {
+        double W[8], M[64];
         for (int v = 0; v < m; ++v) W[v] = W0[(size_t)v * nodes + i];
         ko_maxwellian(P, W, M);
         for (int pop = 0; pop < nv * m; ++pop) f[(size_t)pop * nodes + i] = M[pop];
@@ -771,4 +787,15 @@ int ko_mass(const ko_problem* P, const double* W, double* mass)
         mass[v] = s;
     }
     return 0;
+}
+
+int ko_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
 }

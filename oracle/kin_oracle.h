@@ -106,6 +106,11 @@ int ko_relax(const ko_problem* P, double* f);
 int ko_step(const ko_problem* P, double* f, int nsteps);
 /* Quadrature mass per variable: sum over nodes of cell volume x weights x W. */
 int ko_mass(const ko_problem* P, const double* W, double* mass);
+/* Threads of the parallel loops (subdomains of one iteration, nodes of the
+ * pointwise steps) when built with OpenMP; nthreads <= 0 leaves the count
+ * unchanged.  Returns the count now in use (1 without OpenMP).  Results do
+ * not depend on it. */
+int ko_set_threads(int nthreads);
 
 #ifdef __cplusplus
 }
