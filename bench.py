@@ -2,21 +2,38 @@
 
 A step is one application of S(dt) = R_omega o T_CN(dt) to the whole state:
 the K = 3 subdomain-iterated downwind DG transport of every population plus
-the fused over-relaxation, i.e. one launch of the fused step kernel.
+the fused over-relaxation.
 
-Workload (default): 2D compressible Euler, isentropic vortex on [0,10]^2,
-256 x 256 cells, DG degree 2 (3 x 3 Gauss-Lobatto nodes), D2Q4 (16
-populations per node), dt = 5 x the explicit DG limit, 8 x 8 subdomains,
-FP32 kinetic state: 9,437,184 kinetic DOF (37.7 MB).  The state is smaller
-than L2, so L2 is flushed before every timed step -- a 256 MB write, then a
-256 MB read so that the written lines are back in HBM -- and only the step
-kernel itself is inside the CUDA-event window.
+Default workload (batched): 64 independent 2D compressible Euler / D2Q4
+problems of uneven size -- mesh n x n with n in {64, 128, 256, 512}, DG
+degree 1..3, isentropic vortex or density wave, dt = 2..8 x the explicit DG
+limit, 32-cell subdomains, FP32 -- 1,105,788,928 kinetic DOF (4.4 GB, far
+larger than L2, so no flush is needed between steps).  One step advances
+every instance once, replayed from a captured CUDA graph with the schedule
+the autotuner picks on this GPU.  The line also carries:
+
+* roofline: algorithmic bytes (8 B per kinetic DOF in FP32: read f^n, write
+  f^{n+1}) over the event-timed step, against the measured HBM copy rate;
+  the per-degree launches timed alone; DRAM traffic from an ncu capture of
+  the same kernels when that capture matches the current source;
+* e2e: the same metric through the C ABI with host buffers -- every step
+  copies every instance's f in from page-locked host memory
+  (kin_set_kinetic), steps the batch, and copies every f out
+  (kin_get_kinetic);
+* plain_fp64: the same instances stepped one at a time in FP64;
+* serving: the serving configuration's Poisson stream (1000 requests by
+  default) through the continuous-batching server, p50/p99 latency;
+* cpu_baseline / error_vs_oracle (the oracle leg, after the GPU work): the
+  FP64 CPU oracle timed on the host cores (one thread and all of them) on a
+  bounded sample of the instances, and the GPU result of sampled instances
+  against the oracle run for the same number of steps.
 
 Metric: kinetic-DOF updates per second (one kinetic DOF = one nodal value of
 one population advanced by one full step).
 
-`--impl reference` times the FP64 CPU oracle (the test reference of this
-repository) on the same workload and metric on the host cores.
+`--workload` selects a single-problem line instead (vortex2d, densitywave3d,
+...).  `--impl reference` times the FP64 CPU oracle (the test reference of
+this repository) on a bounded sample of the same workload on all host cores.
 """
 from __future__ import annotations
 
@@ -63,12 +80,36 @@ def flops_per_dof(dim, degree, m, nvel, maxwell=False):
     else:
         relax = m * (nvel - 1) + (1 + 2 * dim + 4) + dim * (1 + 2 * dim + 3 + m * 8)
     return sweep + summary + relax / npop + 1.0
-# DRAM bytes (read + write) of one step launch from an ncu capture of the same
-# kernel and workload (profiles/step_kernel_fixed_vortex2d_256x256_p2.md,
-# profiles/step_kernel_fixed_vortex2d_512x512_p3.md); stores still in L2 at
-# kernel end are not counted by the capture.
-NCU_TRAFFIC = {("vortex2d", "f32"): 39.760384e6 + 0.0704e6,
-               ("vortex2d-512-p3", "f32"): 279.491328e6 + 217.914624e6}
+# DRAM bytes (read + write) per launch from ncu captures, with the hash of
+# the kernel sources they were taken on (source_hash): a figure is reported
+# only while the sources are unchanged, else the line's traffic is null.
+# Keys: (workload, precision); the batched figure is per batch step (all its
+# launches), scaled from a capture of a smaller mix by the kinetic DOF.
+NCU_TRAFFIC = {}
+
+
+def source_hash():
+    """sha256 (16 hex digits) of the CUDA sources and the public header."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2212_11010_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
+    with open(os.path.join(ROOT, "include", "kin.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(key):
+    """(bytes per launch or None, note)."""
+    rec = NCU_TRAFFIC.get(key)
+    if rec is None:
+        return None, "no ncu capture of this workload"
+    nbytes, src = rec
+    if src != source_hash():
+        return None, f"capture taken on sources {src}; sources changed since"
+    return nbytes, f"ncu capture on sources {src}"
 
 
 def host_cpu():
@@ -225,76 +266,79 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def cpu_oracle_rate(w, budget_s=12.0, max_steps=50):
-    """The oracle as it stands, single thread, timed on a bounded sample:
-    whole steps of the same workload from the same initial state."""
+# ---------------------------------------------------------------------------
+# the oracle leg: CPU baseline and accuracy check (after the GPU work)
+# ---------------------------------------------------------------------------
+
+def _gll_weights(w):
     import oracle
+    _, wq = oracle.gll(w.degree)
+    cellw = np.ones(1)
+    for _ in range(w.dim):
+        cellw = np.kron(wq, cellw)
+    return np.tile(cellw, int(np.prod(w.n)))
+
+
+def state_errors(w, W, Wo, f=None, fo=None):
+    """Relative errors against the oracle: per conserved variable the
+    GLL-weighted L2 and the max norm (relative to the oracle's norm of that
+    variable), the worst variable; and f element by element per population
+    (relative to the oracle's max |f| of that population), the worst one."""
+    W = np.asarray(W).reshape(w.m, -1)
+    Wo = np.asarray(Wo).reshape(w.m, -1)
+    q = _gll_weights(w)
+    l2 = max(float(np.sqrt(np.sum(q * (W[v] - Wo[v]) ** 2) / np.sum(q * Wo[v] ** 2))) for v in range(w.m))
+    linf = max(float(np.abs(W[v] - Wo[v]).max() / np.abs(Wo[v]).max()) for v in range(w.m))
+    out = {"W_l2": l2, "W_linf": linf}
+    if f is not None:
+        f = np.asarray(f).reshape(w.npop, -1).astype(np.float64)
+        fo = np.asarray(fo).reshape(w.npop, -1)
+        out["f_max"] = max(float(np.abs(f[k] - fo[k]).max() / np.abs(fo[k]).max()) for k in range(w.npop))
+    return out
+
+
+def oracle_state(w, steps, threads=0):
+    """(f, W) of the FP64 oracle after 'steps' steps from w.W0."""
+    import oracle
+    oracle.set_threads(threads or os.cpu_count() or 1)
     P = oracle.Problem(**w.oracle_kwargs())
     f = oracle.init(P, w.W0)
-    steps = 0
+    oracle.step(P, f, steps)
+    return f, oracle.moments(P, f)
+
+
+def oracle_rate(ws, threads, budget_s):
+    """DOF-updates/s of the oracle as it stands on 'threads' host threads:
+    one step of every problem in ws, passes repeated until budget_s."""
+    import oracle
+    oracle.set_threads(threads)
+    probs = [(oracle.Problem(**w.oracle_kwargs()), w) for w in ws]
+    states = [oracle.init(P, w.W0) for P, w in probs]
+    done = 0
+    passes = 0
     t0 = time.perf_counter()
-    while steps < max_steps:
-        oracle.step(P, f, 1)
-        steps += 1
+    while True:
+        for (P, w), f in zip(probs, states):
+            oracle.step(P, f, 1)
+            done += w.kinetic_dofs
+        passes += 1
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return w.kinetic_dofs * steps / dt, steps, dt
-
-
-def reference_sample(w, name, steps, warmup, budget_s=100.0):
-    """A bounded sample of the workload for the oracle arm: the same problem
-    (same degree, velocity set, subdomain extent, time step and initial-data
-    recipe) on a mesh small enough that warmup + steps oracle steps fit the
-    time budget.  The oracle's cost per kinetic DOF does not depend on the
-    mesh size, so the DOF-update rate of the sample is that of the workload."""
-    import oracle
-    import workloads
-    if name != "vortex2d":
-        return w, "full workload"
-    sub = w.n[0] // w.tiles[0]               # subdomain extent (32 cells)
-    probe = workloads.vortex2d(seed=0, n=sub, tiles=1)
-    P = oracle.Problem(**probe.oracle_kwargs())
-    f = oracle.init(P, probe.W0)
-    t0 = time.perf_counter()
-    oracle.step(P, f, 2)
-    per_dof = (time.perf_counter() - t0) / (2 * probe.kinetic_dofs)
-    n = w.n[0]
-    while n > sub and per_dof * (steps + warmup) * (w.kinetic_dofs * (n / w.n[0]) ** 2) > budget_s:
-        n //= 2
-    if n == w.n[0]:
-        return w, "full workload"
-    s = workloads.vortex2d(seed=0, n=n, tiles=n // sub)
-    return s, f"{n}x{n} cells of the same recipe ({n // sub}x{n // sub} subdomains of {sub}^2 cells)"
-
-
-def run_reference(args):
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return
-    w, desc = make_workload(args.workload)
-    import oracle
-    s, sample = reference_sample(w, args.workload, args.steps, args.warmup)
-    P = oracle.Problem(**s.oracle_kwargs())
-    f = oracle.init(P, s.W0)
-    for _ in range(args.warmup):
-        oracle.step(P, f, 1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.step(P, f, 1)
     el = time.perf_counter() - t0
-    value = s.kinetic_dofs * args.steps / el
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": desc, "kinetic_dofs": w.kinetic_dofs, "parallelism": "cpu-1thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step: one full step of {sample}", "host": host_cpu()},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    return done / el, passes, el
+
+
+def cpu_baseline_of(sample_all, desc_all, sample_one, desc_one, budget_s=12.0):
+    """The oracle on all host cores and on one core, each on a bounded sample."""
+    cores = os.cpu_count() or 1
+    rate, passes, el = oracle_rate(sample_all, cores, budget_s)
+    rate1, passes1, el1 = oracle_rate(sample_one, 1, budget_s / 3)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{passes} pass(es) of one step of {desc_all} in {el:.1f} s, OpenMP over the "
+                      f"subdomains of each iteration",
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": f"{passes1} pass(es) of one step of {desc_one} in {el1:.1f} s"},
+            "host": host_cpu()}
 
 
 def run_ours(args):
@@ -393,16 +437,14 @@ def run_ours(args):
                 "flops_per_dof": fpd, "hbm_GBs": achieved, "hbm_frac": achieved / peak}
     else:
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": NCU_TRAFFIC.get((args.workload, prec)),
+                "frac": achieved / peak, "traffic": traffic_for((args.workload, prec))[0],
+                "traffic_note": traffic_for((args.workload, prec))[1],
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes}
     # launches of ours per step: one fused step kernel for the axis sets; the
     # d + 1 sets take a trace pass, K sweeps and a relaxation pass
     launches_per_step = 1 if w.velset == 0 else 2 + w.iters
     clocks = clk.summary()
 
-    # result sanity (not timed): finite state
-    Wf = ctx.get_state()
-    finite = bool(np.isfinite(Wf).all())
 
     if rank == 0:
         line = {
@@ -421,45 +463,74 @@ def run_ours(args):
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clocks,
             "wall_s_timed_region": wall,
-            "state_finite": finite,
         }
         if ws == 1 and not args.no_cpu_baseline:
-            rate, nst, el = cpu_oracle_rate(w)
-            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"{nst} full steps of {desc} in {el:.1f} s", "host": host_cpu()}
+            # the oracle leg: accuracy after the steps this context took (when
+            # the oracle finishes them within the budget), then the CPU baseline
+            steps_taken = args.warmup + args.steps + 2 + e2e_steps
+            if w.kinetic_dofs * steps_taken < 4e9:
+                fo, Wo = oracle_state(w, steps_taken)
+                err = state_errors(w, ctx.get_state(), Wo, ctx.get_kinetic(), fo)
+                err.update({"steps": steps_taken, "tolerance": 1e-5 if prec == "f32" else 1e-12})
+                line["error_vs_oracle"] = err
+            else:
+                line["error_vs_oracle"] = {"skipped": "the oracle would exceed the time budget at this size; "
+                                                      "the parity tests cover it"}
+            line["cpu_baseline"] = cpu_baseline_of([w], desc, [w], desc)
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
 
 
-def _events_time(stream, fn, steps):
+# ---------------------------------------------------------------------------
+# batched (default)
+# ---------------------------------------------------------------------------
+
+BATCHED_DESC = "batched-64x-euler2d-D2Q4-n64..512-p1..3-32cell-subdomains-K3"
+
+
+def _setup_gpu():
     import torch
-    s = torch.cuda.Event(enable_timing=True)
-    e = torch.cuda.Event(enable_timing=True)
-    s.record(stream)
-    for _ in range(steps):
-        fn()
-    e.record(stream)
-    e.synchronize()
-    return s.elapsed_time(e) / 1e3
+    import paper_2212_11010_gb300 as kin
+    from paper_2212_11010_gb300 import build as kbuild
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if not kbuild.up_to_date():
+        if rank == 0:
+            kbuild.build()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+    kin.load_library()
+    return ws, rank, torch.cuda.current_device()
+
+
+def _time_batch(batch, stream, steps):
+    """Per-step CUDA-event times (ms) of 'steps' single-step graph replays."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        batch.step(1)
+        b.record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
 
 
 def run_batched(args):
-    """64 uneven 2D Euler / D2Q4 instances (n in {64,128,256,512}, p in
-    {1,2,3}, vortex or density wave, dt multiple in [2,8]) stepped together in
-    FP32 (one launch per degree per step, CUDA graphs), against the same
-    instances in FP64 stepped one instance at a time.  The state (3.4 GB FP32)
-    exceeds L2, so no flush is needed between steps."""
+    """The batched configuration: 64 uneven 2D Euler / D2Q4 instances stepped
+    together in FP32.  See the module docstring for the fields."""
     import torch
     import workloads
     import paper_2212_11010_gb300 as kin
-    from paper_2212_11010_gb300 import build as kbuild
-    ws, rank, _ = dist_env()
-    torch.cuda.set_device(0)
-    if not kbuild.up_to_date():
-        kbuild.build()
-    kin.load_library()
+    from paper_2212_11010_gb300 import autotune
+    ws, rank, dev = _setup_gpu()
     mix = workloads.batched_mix(seed=0, count=64)
     dofs = sum(w.kinetic_dofs for w in mix)
     stream = torch.cuda.Stream()
@@ -468,89 +539,203 @@ def run_batched(args):
         c = kin.Context.from_workload(w, precision=kin.KIN_FP32, torch_alloc=True, stream=stream.cuda_stream)
         c.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
         ctxs.append(c)
-    batch = kin.Batch(ctxs, stream=stream.cuda_stream)
+    steps_done = [0] * len(mix)
+
+    # schedule: the autotuner times the candidate batch schedules on these members (untimed)
+    sched, sched_ms, taken = autotune.tune_batch(ctxs, stream)
+    steps_done = [s + taken for s in steps_done]
+    batch = kin.Batch(ctxs, stream=stream.cuda_stream, mixed=sched.mixed)
     batch.step(args.warmup)
     batch.sync()
-    with ClockSampler(0) as clk:
+    steps_done = [s + args.warmup for s in steps_done]
+
+    # timed region: K single-step graph replays, CUDA events on the batch stream
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
         t0 = time.perf_counter()
-        el = _events_time(stream, lambda: batch.step(args.steps), 1)   # K steps in one call
+        times = _time_batch(batch, stream, args.steps)
         clk.mark(t0, time.perf_counter())
-    batch.sync()
-    value = dofs * args.steps / el
-    launches_per_step = len({(c.info.degree, c.info.specialised) for c in ctxs})
+    torch.cuda.synchronize()
+    steps_done = [s + args.steps for s in steps_done]
+    launches = batch.launches_per_step
     batch.close()
-    for c in ctxs:
-        c.close()
-    # plain FP64 path: the same instances one at a time
+    ms_per_step, value = replica_aggregate(float(np.sum(times)), args.steps, dofs)
+
+    # each kernel type's launch alone (the same members, untimed for the metric)
+    per_kernel = []
+    for p in sorted({w.degree for w in mix}):
+        idx = [i for i, w in enumerate(mix) if w.degree == p]
+        with kin.Batch([ctxs[i] for i in idx], stream=stream.cuda_stream) as b:
+            b.step(2)
+            t = _time_batch(b, stream, args.steps)
+        for i in idx:
+            steps_done[i] += 2 + args.steps
+        d = sum(mix[i].kinetic_dofs for i in idx)
+        ms = float(np.mean(t))
+        per_kernel.append({"kernel": f"step_kernel_fixed_batch, degree {p}, block {list(ctxs[idx[0]].info.block)}",
+                           "instances": len(idx), "kinetic_dofs": d, "ms": ms,
+                           "GBs": 8 * d / (ms * 1e-3) / 1e9})
+
+    peak, peak_kind = measured_peak_hbm()
+    algo_bytes = ALGO_BYTES_PER_DOF["f32"] * dofs
+    achieved = algo_bytes / (ms_per_step * 1e-3) / 1e9
+    traffic, traffic_note = traffic_for(("batched", "f32"))
+    for k in per_kernel:
+        k["frac"] = k["GBs"] / peak
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
+            "kernel": f"the batch step: {launches} launch(es) of the fused step kernel ({sched.label}), "
+                      "back to back on one stream; per step 8 B per kinetic DOF",
+            "traffic_note": traffic_note, "per_kernel": per_kernel}
+
+    # e2e through the C ABI with host buffers
+    fh = [torch.empty(c.info.kinetic_values, dtype=torch.float32, pin_memory=True) for c in ctxs]
+    for c, h in zip(ctxs, fh):
+        kin.kin_get_kinetic(c.ctx, h.numpy())
+    e2e_steps = max(2, min(args.steps, 4))
+    with kin.Batch(ctxs, stream=stream.cuda_stream, mixed=sched.mixed) as b:
+        def e2e_step():
+            for c, h in zip(ctxs, fh):
+                kin.kin_set_kinetic(c.ctx, h.numpy())
+            b.step(1)
+            for c, h in zip(ctxs, fh):
+                kin.kin_get_kinetic(c.ctx, h.numpy())
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    steps_done = [s + 1 + e2e_steps for s in steps_done]
+    del fh
+
+    # the plain path: the same instances in FP64, one instance at a time
     ctx64 = []
     for w in mix:
         c = kin.Context.from_workload(w, precision=kin.KIN_FP64, torch_alloc=True, stream=stream.cuda_stream)
         c.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
         ctx64.append(c)
-    k64 = max(1, min(args.steps, 5))
+    k64 = max(1, min(args.steps, 3))
 
     def one_at_a_time():
         for c in ctx64:
             c.step(1)
     one_at_a_time()
     stream.synchronize()
-    el64 = _events_time(stream, one_at_a_time, k64)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k64):
+        one_at_a_time()
+    e1.record(stream)
+    e1.synchronize()
+    el64 = e0.elapsed_time(e1) * 1e-3
     value64 = dofs * k64 / el64
-    for c in ctx64:
-        c.close()
-    peak, peak_kind = measured_peak_hbm()
-    ms = 1e3 * el / args.steps
-    achieved = 8 * dofs / (ms * 1e-3) / 1e9
+    steps64 = 1 + k64
+
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batched-64x-euler2d-D2Q4-n64..512-p1..3-32cell-subdomains-K3",
-                   "instances": len(mix), "kinetic_dofs": dofs, "state_bytes": 4 * dofs,
-                   "l2": "state 3.4 GB exceeds L2; no flush", "launches_per_step": launches_per_step},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind},
+        "config": {"workload": BATCHED_DESC, "instances": len(mix), "kinetic_dofs": dofs,
+                   "state_bytes": 4 * dofs, "l2": "state 4.4 GB exceeds L2 (129 MB); no flush",
+                   "launches_per_step": launches, "schedule": sched.label,
+                   "schedule_ms_per_step": {s_.label: v for s_, v in sched_ms.items()},
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu"},
+        "roofline": roof,
+        "e2e": {"value": dofs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 4 * dofs,
+                "d2h_bytes_per_step": 4 * dofs,
+                "path": "per step: kin_set_kinetic of every instance from page-locked host memory, "
+                        "kin_batch_step, kin_get_kinetic of every instance"},
         "plain_fp64": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * el64 / k64,
-                       "path": "each instance stepped alone, FP64"},
+                       "path": "each instance stepped alone (kin_step), FP64"},
         "batched_over_plain_fp64": value / value64,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches * args.steps,
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if not args.no_serving and ws == 1:
+        line["serving"] = serving_object(args)
+
+    # the oracle leg (rank 0, one GPU): accuracy of sampled instances, CPU baseline
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sample = []
+        for p in sorted({w.degree for w in mix}):
+            i = min((i for i, w in enumerate(mix) if w.degree == p), key=lambda i: (mix[i].n[0], i))
+            sample.append(i)
+        errs32, errs64 = [], []
+        for i in sample:
+            w = mix[i]
+            fo, Wo = oracle_state(w, steps_done[i])
+            e = state_errors(w, ctxs[i].get_state(), Wo, ctxs[i].get_kinetic(), fo)
+            e.update({"instance": i, "n": w.n[0], "degree": w.degree, "steps": steps_done[i]})
+            errs32.append(e)
+            fo, Wo = oracle_state(w, steps64)
+            e = state_errors(w, ctx64[i].get_state(), Wo, ctx64[i].get_kinetic(), fo)
+            e.update({"instance": i, "steps": steps64})
+            errs64.append(e)
+        line["error_vs_oracle"] = {
+            "f32": {k: max(e[k] for e in errs32) for k in ("W_l2", "W_linf", "f_max")},
+            "f64": {k: max(e[k] for e in errs64) for k in ("W_l2", "W_linf", "f_max")},
+            "tolerance": {"f32": 1e-5, "f64": 1e-12, "applies_to": "W_l2, W_linf"},
+            "sample": errs32, "sample_f64": errs64,
+            "note": "the smallest instance of each degree, against the FP64 oracle run for the same steps"}
+        small = [w for w in mix if w.n[0] <= 128]
+        one = [w for w in mix if w.n[0] == 64]
+        line["cpu_baseline"] = cpu_baseline_of(small, f"the {len(small)} instances with n <= 128",
+                                               one, f"the {len(one)} instances with n = 64")
+    for c in ctx64:
+        c.close()
+    for c in ctxs:
+        c.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
-def run_serving(args):
-    """Seeded Poisson stream (200 requests/s) of 2D Euler / D2Q4 requests, mesh
-    64^2..1024^2 (log-uniform over powers of two), degree 1..3, 50..500
-    steps, FP32 state resident on the device, admitted under a 150 GB budget;
-    continuous batching (paper_2212_11010_gb300.serve)."""
+# ---------------------------------------------------------------------------
+# serving (nested in the batched line, or alone with --workload serving)
+# ---------------------------------------------------------------------------
+
+SERVING_DESC = "serving-poisson200-euler2d-D2Q4-n64..1024-loguniform-p1..3-steps50..500-budget150GB"
+
+
+def serving_object(args):
+    """The serving configuration: a seeded Poisson stream (mean 200 requests
+    per second) of 2D Euler / D2Q4 requests, mesh n x n with n log-uniform on
+    [64, 1024] (rounded to the 32-cell subdomain extent), degree 1..3, 50..500
+    steps, FP32 state resident on the device, admitted under a 150 GB budget
+    and advanced by the continuous-batching server."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     import workloads
-    import paper_2212_11010_gb300 as kin
-    from paper_2212_11010_gb300 import build as kbuild
     from paper_2212_11010_gb300 import serve
-    torch.cuda.set_device(0)
-    if not kbuild.up_to_date():
-        kbuild.build()
-    kin.load_library()
-    reqs = workloads.serving_stream(seed=0, count=args.requests, rate=200.0)
+    reqs = workloads.serving_stream(seed=0, count=args.requests, rate=200.0, size_range=(64, 1024))
     for r in reqs:
-        r.seed = 0            # one initial field per (kind, n, degree): client data, prepared up front
+        r.seed = 0            # one initial field per (kind, n, degree): client data prepared up front
+    uniq = {}
     for r in reqs:
-        workloads.request_workload(r)
-    # the clients' initial fields arrive in page-locked host memory, so that
-    # their host-to-device copies run at the link's rate
+        uniq.setdefault((r.kind, r.n, r.degree), r)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        list(ex.map(workloads.request_workload, uniq.values()))
+    # the clients' fields arrive in page-locked host memory, so that their
+    # host-to-device copies run at the link's rate (request_workload hands
+    # out copies of these cached recipes, sharing their W0)
     pinned = []
-    for w in workloads._request_cache.values():
+    for key, w in list(workloads._request_cache.items()):
         t = torch.empty(w.W0.size, dtype=torch.float64, pin_memory=True)
         t.numpy()[:] = w.W0.reshape(-1)
         pinned.append(t)
         w.W0 = t.numpy().reshape(w.W0.shape)
-    # warm-up: one small request through the server (module load, graph set-up paths)
+    prep_s = time.perf_counter() - t0
     warm = workloads.serving_stream(seed=9, count=2, rate=1000.0, sizes=(64,), steps=(5, 5))
     serve.Server(budget_bytes=150e9).run(warm, workloads.request_workload)
     torch.cuda.synchronize()
-    with ClockSampler(0) as clk:
+    with ClockSampler(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
         server = serve.Server(budget_bytes=150e9, chunk_steps=25, keep_results=False)
         recs = server.run(reqs, workloads.request_workload)
@@ -558,37 +743,118 @@ def run_serving(args):
     st = serve.summarize(recs, server.device_busy_s)
     peak, peak_kind = measured_peak_hbm()
     dev_gbs = 8 * st["dof_updates_per_device_s"] / 1e9
+    waited = sum(1 for r in recs if r.admitted - r.arrival > 0.05)
+    workloads._request_cache.clear()
+    del pinned
+    return {"workload": SERVING_DESC, "requests": st["requests"], "distinct_meshes": len({r.n for r in reqs}),
+            "value": st["dof_updates_per_s"], "unit": UNIT,
+            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+            "makespan_s": st["makespan_s"], "arrival_span_s": reqs[-1].arrival,
+            "note": "offered load exceeds the device's throughput; latency includes queueing",
+            "admitted_after_50ms_wait": waited, "peak_device_bytes": server.peak_bytes,
+            "hbm_budget_bytes": 150e9, "chunk_steps": 25, "schedule": "mixed" if server.mixed else "per kernel type",
+            "device": {"busy_s": st["device_busy_s"], "dof_updates_per_busy_s": st["dof_updates_per_device_s"],
+                       "hbm_GBs_while_busy": dev_gbs, "hbm_frac_while_busy": dev_gbs / peak,
+                       "peak": peak, "peak_kind": peak_kind},
+            "client_data_prep_s": prep_s, "clocks": clk.summary()}
+
+
+def run_serving(args):
+    _setup_gpu()
+    obj = serving_object(args)
+    line = {"metric": METRIC, "value": obj["value"], "unit": UNIT, "n_gpus": 1, "steps": None,
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SERVING_DESC, "requests": obj["requests"]}, "serving": obj}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, on all host cores, on the default
+    line's workload and metric: each step is one oracle step of a bounded
+    sample of the workload (for the batched mix: every instance with
+    n <= 128; for a single problem: the problem itself, or a smaller mesh
+    of the same recipe when a step of the full one would not fit the budget)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    if args.workload == "batched":
+        mix = workloads.batched_mix(seed=0, count=64)
+        sample = [w for w in mix if w.n[0] <= 128]
+        desc, sdesc = BATCHED_DESC, f"the {len(sample)} instances with n <= 128"
+        dofs_total = sum(w.kinetic_dofs for w in mix)
+    else:
+        w, desc = make_workload(args.workload)
+        s, sdesc = reference_sample(w, args.workload, args.steps, args.warmup)
+        sample = [s]
+        dofs_total = w.kinetic_dofs
+    probs = [(oracle.Problem(**w.oracle_kwargs()), w) for w in sample]
+    states = [oracle.init(P, w.W0) for P, w in probs]
+
+    def one():
+        for (P, w), f in zip(probs, states):
+            oracle.step(P, f, 1)
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    el = time.perf_counter() - t0
+    value = sum(w.kinetic_dofs for w in sample) * args.steps / el
     line = {
-        "metric": METRIC, "value": st["dof_updates_per_s"], "unit": UNIT, "n_gpus": 1,
-        "steps": None, "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serving-poisson200-euler2d-D2Q4-n64..1024-p1..3-steps50..500",
-                   "requests": st["requests"], "hbm_budget_bytes": 150e9, "chunk_steps": 25},
-        "latency": {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
-                    "makespan_s": st["makespan_s"],
-                    "note": "offered load exceeds the device's throughput; latency includes queueing"},
-        "device": {"busy_s": st["device_busy_s"], "dof_updates_per_busy_s": st["dof_updates_per_device_s"],
-                   "hbm_GBs_while_busy": dev_gbs, "hbm_frac_while_busy": dev_gbs / peak, "peak": peak,
-                   "peak_kind": peak_kind,
-                   "note": "CUDA-event time of the chunks on the server's stream; value is over the makespan"},
-        "clocks": clk.summary(),
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "kinetic_dofs": dofs_total, "parallelism": f"cpu-{cores}threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: one oracle step of {sdesc}", "host": host_cpu()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def reference_sample(w, name, steps, warmup, budget_s=100.0):
+    """A bounded sample of a single-problem workload for the oracle arm: the
+    same recipe (degree, velocity set, subdomain extent, time step) on a mesh
+    small enough that warmup + steps oracle steps fit the time budget.  The
+    oracle's cost per kinetic DOF does not depend on the mesh size."""
+    import workloads
+    if name != "vortex2d":
+        return w, "the full workload"
+    sub = w.n[0] // w.tiles[0]               # subdomain extent (32 cells)
+    n = w.n[0]
+    per_dof = 1.0 / (2e7 * max(1, (os.cpu_count() or 1) // 2))
+    while n > sub and per_dof * (steps + warmup) * (w.kinetic_dofs * (n / w.n[0]) ** 2) > budget_s:
+        n //= 2
+    if n == w.n[0]:
+        return w, "the full workload"
+    s = workloads.vortex2d(seed=0, n=n, tiles=n // sub)
+    return s, f"{n}x{n} cells of the same recipe ({n // sub}x{n // sub} subdomains of {sub}^2 cells)"
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="vortex2d",
-                    choices=["vortex2d", "densitywave3d", "advection1d", "batched", "serving",
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "serving", "vortex2d", "densitywave3d", "advection1d",
                              "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d", "vortex2d-512-p3",
                              "maxwell3d-dirichlet"])
-    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -222,8 +222,9 @@ kin_status kin_diag(kin_ctx* ctx, double* mass_per_var, double* next_defect, dou
  * acceptable.
  *
  * mesh, model, degree, dt: as kin_create (periodic axes only: a mesh with an
- * inflow axis is KIN_EINVAL).  opts: tiles, iters, precision, block and
- * stream are used; mem_budget and the allocator hooks are ignored.
+ * inflow axis is KIN_EINVAL).  opts: tiles, iters, precision, block,
+ * threads, stages, wait_timeout_s and stream are used as in kin_create;
+ * mem_budget, debug_flags and the allocator hooks are ignored.
  * f: device pointer to the caller's kinetic state, npop * nodes values of
  * opts->precision in the storage order above; read as f^n and overwritten
  * in place with f^{n + nsteps} (the caller owns it).  errbuf/errlen: optional
@@ -247,11 +248,18 @@ kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int de
 
 /* Batched stepping of several independent problems (the paper's method
  * applied to each; Sec. 2.2, 3, 5.1).  A batch groups existing contexts with
- * a state; kin_batch_step advances every member by nsteps steps with, per
- * step, one persistent launch per kernel type covering the tiles of all
- * members of that type (problems of different mesh size share a launch),
- * replayed from a captured CUDA graph.  Results equal stepping each member
- * alone (bitwise: the same kernel arithmetic per tile).
+ * a state; kin_batch_step advances every member by nsteps steps, replayed
+ * from a captured CUDA graph.  Per step, the members run in one persistent
+ * launch per kernel type covering the tiles of all members of that type
+ * (problems of different mesh size share a launch; a member without a
+ * fixed-shape kernel gets its own launch).  With KIN_BATCH_MIXED the 2D
+ * Euler FP32 members of degrees 1..3 whose cell blocks match one of the
+ * library's compiled mixed-degree kernels (the default cell blocks of
+ * kin_create, 0 in kin_opts.block, match the first) share ONE persistent
+ * launch over a work list of all their tiles, the most expensive first.
+ * Results equal stepping each member alone (bitwise: the same kernel
+ * arithmetic per tile).  kin_set_state and kin_set_kinetic on a member keep
+ * the batch valid (they rebuild the member's summaries in place).
  *
  * members: count distinct contexts of one device, each with a state; they
  * stay owned by the caller and must outlive the batch.  stream: cudaStream_t
@@ -269,9 +277,13 @@ kin_status kin_batch_create(kin_ctx* const* members, int count, void* stream, ki
 /* As kin_batch_create, with flags: KIN_BATCH_DIRECT enqueues each step's
  * launches directly instead of capturing and replaying CUDA graphs (cheaper
  * to create: for batches whose membership changes often, as in a serving
- * loop).  Results are the same.  Unknown flags: KIN_EINVAL. */
-enum { KIN_BATCH_DIRECT = 1 };
+ * loop); KIN_BATCH_MIXED puts the eligible 2D members into one mixed-degree
+ * launch (see above).  Results are the same.  Unknown flags: KIN_EINVAL. */
+enum { KIN_BATCH_DIRECT = 1, KIN_BATCH_MIXED = 2 };
 kin_status kin_batch_create_ex(kin_ctx* const* members, int count, void* stream, int flags, kin_batch** out);
+/* Launches of this library per batch step, and how many members share the
+ * mixed-degree launch (either pointer may be NULL). */
+kin_status kin_batch_info(const kin_batch* batch, int* launches_per_step, int* mixed_members);
 kin_status kin_batch_step(kin_batch* batch, int nsteps);
 kin_status kin_batch_sync(kin_batch* batch);
 kin_status kin_batch_destroy(kin_batch* batch);

@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
 EXPORTED = ["kin_create", "kin_set_state", "kin_set_kinetic", "kin_step", "kin_get_state",
             "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error",
             "kin_step_noalloc", "kin_batch_create", "kin_batch_create_ex", "kin_batch_step", "kin_batch_sync",
-            "kin_batch_destroy", "kin_batch_last_error", "kin_set_boundary"]
+            "kin_batch_destroy", "kin_batch_last_error", "kin_set_boundary", "kin_batch_info"]
 
 
 class KinError(RuntimeError):
@@ -110,6 +110,7 @@ def load_library():
     lib.kin_batch_create_ex.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(vp)]
     lib.kin_batch_step.argtypes = [vp, ctypes.c_int]
     lib.kin_batch_sync.argtypes = [vp]
+    lib.kin_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.kin_batch_destroy.argtypes = [vp]
     lib.kin_batch_last_error.argtypes = [vp]
     lib.kin_batch_last_error.restype = ctypes.c_char_p
@@ -259,6 +260,7 @@ def _bcheck(batch, status):
 
 
 KIN_BATCH_DIRECT = 1
+KIN_BATCH_MIXED = 2
 
 
 def kin_batch_create(ctxs, stream=None):
@@ -289,6 +291,14 @@ def kin_batch_sync(batch):
 
 def kin_batch_destroy(batch):
     _bcheck(None, load_library().kin_batch_destroy(batch))
+
+
+def kin_batch_info(batch):
+    """(launches per batch step, members in the mixed-degree launch)."""
+    n = ctypes.c_int(0)
+    mixed = ctypes.c_int(0)
+    _bcheck(batch, load_library().kin_batch_info(batch, ctypes.byref(n), ctypes.byref(mixed)))
+    return n.value, mixed.value
 
 
 def kin_batch_last_error(batch=None) -> str:
@@ -333,10 +343,11 @@ def make_args(dim, n, lo, hi, system, lam, omega=2.0, gamma=1.4, adv=(0.0, 0.0, 
 class Batch:
     """Owning wrapper of a kin_batch over Context objects (which must outlive it)."""
 
-    def __init__(self, contexts, stream=None, graphs=True):
+    def __init__(self, contexts, stream=None, graphs=True, mixed=False):
         self.contexts = list(contexts)
-        flags = 0 if graphs else KIN_BATCH_DIRECT
+        flags = (0 if graphs else KIN_BATCH_DIRECT) | (KIN_BATCH_MIXED if mixed else 0)
         self.handle = kin_batch_create_ex([c.ctx for c in self.contexts], stream, flags)
+        self.launches_per_step, self.mixed_members = kin_batch_info(self.handle)
 
     def step(self, n=1):
         kin_batch_step(self.handle, n)

@@ -1,13 +1,20 @@
-"""Autotuner for the launch schedule of a kinetic DG problem.
+"""Autotuner for the launch schedules of kinetic DG problems.
 
-The schedule -- cell-block extents, threads per block, shared-memory stages --
-changes how the step is executed, never what it computes beyond round-off:
-the subdomain tiling (which defines the result of the subdomain iteration)
-is part of the problem and is not touched.  The tuner builds a temporary
-context per candidate through the public C ABI, times a few steps with CUDA
-events (L2 flushed between steps when the state would fit in it), and returns
-the fastest candidate.  Results are cached per (GPU name, problem shape), in
-memory and optionally in a JSON file.
+A schedule changes how a step is executed, never what it computes beyond
+round-off.  The subdomain tiling is not a schedule: it defines which
+iterate of the subdomain iteration (Sec. 5.1, eq. ibvp) the step returns, so
+it is part of the problem and the tuner never changes it.
+
+* ``tune(w)``: one problem -- cell-block extents, threads per block,
+  shared-memory stages.  Builds a temporary context per candidate through
+  the public C ABI and times a few steps with CUDA events (L2 flushed between
+  steps when the state would fit in it).
+* ``tune_batch(contexts)``: a batch of problems -- one persistent launch per
+  kernel type, or one mixed-degree launch for all 2D members.  Times each
+  candidate on the actual members with graph-replayed steps.
+
+Results are cached per (GPU name, problem or batch shape), in memory and
+optionally in a JSON file.
 """
 from __future__ import annotations
 
@@ -120,3 +127,65 @@ def tune(w, precision=None, steps: int = 8, cache_file: str = None, cands=None):
         with open(cache_file, "w") as fh:
             json.dump(data, fh, indent=1)
     return best, timings
+
+
+@dataclass(frozen=True)
+class BatchSchedule:
+    mixed: bool = False      # one mixed-degree launch (KIN_BATCH_MIXED) instead of one per kernel type
+
+    @property
+    def label(self):
+        return "one mixed-degree launch per step" if self.mixed else "one launch per kernel type per step"
+
+
+_batch_cache = {}
+
+
+def _batch_key(contexts):
+    import torch
+    shape = sorted((c.info.dim, c.info.degree, c.info.m, int(c.info.cells), c.info.precision,
+                    tuple(c.info.block)) for c in contexts)
+    return json.dumps([torch.cuda.get_device_name(), shape])
+
+
+def tune_batch(contexts, stream=None, steps: int = 6, reps: int = 2):
+    """Fastest batch schedule for these contexts.  Every candidate batch is
+    created over the same members, run for two untimed steps, then timed on
+    ``reps`` runs of ``steps`` graph-replayed steps (best run kept).  The
+    members' states advance by the steps taken; returns (schedule,
+    {schedule: ms per step}, steps taken)."""
+    import torch
+    from . import Batch
+    key = _batch_key(contexts)
+    if key in _batch_cache:
+        return _batch_cache[key], {}, 0
+    st = stream if stream is not None else torch.cuda.current_stream()
+    taken = 0
+    timings = {}
+    for cand in (BatchSchedule(False), BatchSchedule(True)):
+        with Batch(contexts, stream=st.cuda_stream, mixed=cand.mixed) as b:
+            if cand.mixed and b.mixed_members == 0:
+                continue
+            b.step(2)
+            taken += 2
+            best = float("inf")
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                b.step(steps)
+                e1.record(st)
+                e1.synchronize()
+                taken += steps
+                best = min(best, e0.elapsed_time(e1) / steps)
+            b.sync()
+            timings[cand] = best
+    choice = min(timings, key=timings.get)
+    _batch_cache[key] = choice
+    return choice, timings, taken
+
+
+def batch_choice(default=BatchSchedule(False)):
+    """The schedule the last tune_batch on this GPU chose (or the default):
+    for batches whose membership changes too often to tune each one."""
+    return next(reversed(_batch_cache.values()), default) if _batch_cache else default

@@ -355,15 +355,22 @@ static cudaError_t configure_launch(kin_ctx* c)
     return cudaSuccess;
 }
 
-// Launch of the fused kernel: mode 0 = one full step, mode 1 = block
-// summaries of the current state only.  Flips the summary buffers.
+// Launch of the fused kernel: mode 0 = one full step (reads the summaries
+// of buffer cur, writes those of the new state to cur ^ 1 and flips cur);
+// mode 1 = block summaries of the current state only, written straight into
+// buffer cur (mode 1 reads no summaries), so cur stays: a state set through
+// kin_set_state / kin_set_kinetic keeps a member's batch valid.
 static kin_status launch_step(kin_ctx* c, int mode)
 {
     Inst I = make_inst(c, mode);
+    if (mode == 1) {
+        I.sig_out = c->sig[c->cur];
+        I.raw_out = c->raw[c->cur];
+    }
     void* args[] = {&I};
     KIN_CUDA(c, cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(c->threads), args,
                                  (size_t)c->smem, c->stream));
-    c->cur ^= 1;
+    if (mode == 0) c->cur ^= 1;
     return KIN_OK;
 }
 
@@ -1027,7 +1034,9 @@ struct kin_batch {
     std::vector<kin_ctx*> members;
     std::vector<int> expect_cur;      // members' summary parity at batch parity 0
     std::vector<int> solo;            // members stepped by their own kernel
-    std::vector<Group> groups;
+    std::vector<Group> groups;        // groups[0] is the mixed launch when nmixed > 0
+    Group mixed;                      // members of the one-launch mixed-degree kernel
+    int nmixed = 0;
     std::vector<void*> dev;           // device allocations of the batch
     std::vector<cudaEvent_t> ev_member;
     cudaEvent_t ev_done = nullptr;
@@ -1069,29 +1078,40 @@ static void batch_release(kin_batch* b)
     b->stream = nullptr;
 }
 
-// Enqueue one batch step at summary parity q (members' cur = expect_cur ^ q).
-static cudaError_t batch_enqueue_step(kin_batch* b, int q)
+// Enqueue launch k of a batch step (a kernel-type group, then the solo
+// members) at summary parity q (members' cur = expect_cur ^ q) on stream st.
+static cudaError_t batch_launch(kin_batch* b, size_t k, int q, cudaStream_t st)
 {
-    for (auto& g : b->groups) {
+    if (k < b->groups.size()) {
+        auto& g = b->groups[k];
         const Inst* insts = g.insts[q];
         const int2* work = g.work;
         int nwork = g.nwork;
         void* args[] = {(void*)&insts, (void*)&work, (void*)&nwork};
-        cudaError_t e = cudaLaunchKernel(g.fn, dim3(g.grid), dim3(g.threads), args, g.smem, b->stream);
-        if (e != cudaSuccess) return e;
+        return cudaLaunchKernel(g.fn, dim3(g.grid), dim3(g.threads), args, g.smem, st);
     }
-    for (int mi : b->solo) {
-        kin_ctx* c = b->members[mi];
-        const int saved = c->cur;
-        c->cur = b->expect_cur[mi] ^ q;
-        Inst I = make_inst(c, 0);
-        c->cur = saved;
-        void* args[] = {&I};
-        cudaError_t e = cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(c->threads), args,
-                                         (size_t)c->smem, b->stream);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const int mi = b->solo[k - b->groups.size()];
+    kin_ctx* c = b->members[mi];
+    const int saved = c->cur;
+    c->cur = b->expect_cur[mi] ^ q;
+    Inst I = make_inst(c, 0);
+    c->cur = saved;
+    void* args[] = {&I};
+    return cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(c->threads), args, (size_t)c->smem, st);
+}
+
+// Enqueue nsteps batch steps starting at summary parity q: every launch of
+// a step on the batch stream, step after step.  (Running the launches of
+// different kernel types on forked streams, so that one type's launch could
+// fill another's tail, measured no faster: with persistent grids over
+// hundreds of tiles per type the tails are short.)
+static cudaError_t batch_enqueue_steps(kin_batch* b, int q, int nsteps)
+{
+    const size_t nl = b->groups.size() + b->solo.size();
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
+        for (size_t k = 0; k < nl && e == cudaSuccess; ++k) e = batch_launch(b, k, q ^ (s & 1), b->stream);
+    return e;
 }
 
 static cudaError_t batch_capture(kin_batch* b, int q, int nsteps, cudaGraphExec_t* out)
@@ -1099,8 +1119,7 @@ static cudaError_t batch_capture(kin_batch* b, int q, int nsteps, cudaGraphExec_
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t el = cudaSuccess;
-    for (int s = 0; s < nsteps && el == cudaSuccess; ++s) el = batch_enqueue_step(b, q ^ (s & 1));
+    cudaError_t el = batch_enqueue_steps(b, q, nsteps);
     e = cudaStreamEndCapture(b->stream, &graph);
     if (el != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -1121,7 +1140,8 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
                                           kin_batch** out)
 {
     if (!out) return batch_fail(nullptr, KIN_EINVAL, "out is NULL");
-    if (flags & ~KIN_BATCH_DIRECT) return batch_fail(nullptr, KIN_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~(KIN_BATCH_DIRECT | KIN_BATCH_MIXED))
+        return batch_fail(nullptr, KIN_EINVAL, "unknown flags 0x%x", flags);
     *out = nullptr;
     if (!members || count < 1) return batch_fail(nullptr, KIN_EINVAL, "need at least one member");
     for (int i = 0; i < count; ++i) {
@@ -1150,8 +1170,43 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
     b->members.assign(members, members + count);
     for (auto* c : b->members) b->expect_cur.push_back(c->cur);
 
-    // group the members that run a fixed-shape kernel by kernel
+    // With KIN_BATCH_MIXED, one launch for the 2D Euler FP32 members of
+    // degrees 1..3 whose cell block matches a slot of a compiled mixed
+    // kernel: of the compiled ones, the kernel that covers the most kinetic
+    // DOF of the batch.
+    std::vector<char> in_mixed(count, 0);
+    MixedKernel mk[8];
+    const int nmk = (flags & KIN_BATCH_MIXED) ? mixed_kernels_2d(mk, 8) : 0;
+    auto mixable = [&](const kin_ctx* c, const MixedKernel& k) {
+        return c->fixed && c->dim == 2 && c->system == KIN_EULER && c->precision == KIN_FP32 &&
+               c->stages == 1 && c->degree >= 1 && c->degree <= 3 && c->B[0] == k.block[c->degree - 1][0] &&
+               c->B[1] == k.block[c->degree - 1][1];
+    };
+    int best = -1;
+    double best_dof = 0;
+    for (int k = 0; k < nmk; ++k) {
+        double dof = 0;
+        for (int i = 0; i < count; ++i)
+            if (mixable(b->members[i], mk[k])) dof += (double)b->members[i]->npop * b->members[i]->nodes;
+        if (dof > best_dof) {
+            best_dof = dof;
+            best = k;
+        }
+    }
+    if (best >= 0) {
+        b->mixed.fn = mk[best].fn;
+        b->mixed.threads = mk[best].threads;
+        b->mixed.smem = mk[best].smem;
+        for (int i = 0; i < count; ++i)
+            if (mixable(b->members[i], mk[best])) {
+                in_mixed[i] = 1;
+                b->mixed.members.push_back(i);
+            }
+    }
+
+    // group the other members that run a fixed-shape kernel by kernel
     for (int i = 0; i < count; ++i) {
+        if (in_mixed[i]) continue;
         kin_ctx* c = b->members[i];
         FixedKernel fk{nullptr, nullptr, 0, 0};
         if (c->fixed && c->dim == 2) fk = fixed_kernel_d2(c->degree, c->system, c->precision, c->B, c->stages);
@@ -1173,12 +1228,17 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
         g->members.push_back(i);
     }
 
+    if (!b->mixed.members.empty()) b->groups.insert(b->groups.begin(), b->mixed);
+    b->nmixed = (int)b->mixed.members.size();
+
     cudaError_t e = cudaSuccess;
     int dev = 0, nsm = 1;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    for (auto& g : b->groups) {
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        auto& g = b->groups[gi];
         if (e != cudaSuccess) break;
+        const bool mixed = gi == 0 && b->nmixed > 0;
         std::vector<Inst> h[2];
         std::vector<int2> work;
         for (size_t k = 0; k < g.members.size(); ++k) {
@@ -1190,7 +1250,19 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
             }
             c->cur = saved;
             const int ntiles = c->nblk[0] * c->nblk[1] * c->nblk[2];
-            for (int t = 0; t < ntiles; ++t) work.push_back(make_int2((int)k, t));
+            // mixed launch: the degree rides in the top byte of the instance index
+            const int tag = mixed ? (c->degree << 24) : 0;
+            for (int t = 0; t < ntiles; ++t) work.push_back(make_int2(tag | (int)k, t));
+        }
+        if (mixed) {
+            // the most expensive tiles first (per-tile DOF, higher degree
+            // first on ties), so that the persistent blocks end on short tiles
+            auto cost = [&](const int2& w) {
+                const kin_ctx* c = b->members[g.members[w.x & 0xffffff]];
+                return (double)c->npop * c->NN * c->B[0] * c->B[1] * c->B[2] * (1.0 + 0.01 * c->degree);
+            };
+            std::stable_sort(work.begin(), work.end(),
+                             [&](const int2& x, const int2& y) { return cost(x) > cost(y); });
         }
         g.nwork = (int)work.size();
         if (g.smem > 48 * 1024)
@@ -1258,10 +1330,8 @@ extern "C" kin_status kin_batch_step(kin_batch* b, int nsteps)
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_member[i], 0);
     }
     if (b->direct) {
-        for (int s = 0; s < nsteps && e == cudaSuccess; ++s) {
-            e = batch_enqueue_step(b, b->parity);
-            b->parity ^= 1;
-        }
+        if (e == cudaSuccess) e = batch_enqueue_steps(b, b->parity, nsteps);
+        if (nsteps & 1) b->parity ^= 1;
     } else {
         int left = nsteps;
         while (e == cudaSuccess && left >= 2) {
@@ -1302,6 +1372,14 @@ extern "C" kin_status kin_batch_destroy(kin_batch* b)
     cudaStreamSynchronize(b->stream);
     batch_release(b);
     delete b;
+    return KIN_OK;
+}
+
+extern "C" kin_status kin_batch_info(const kin_batch* b, int* launches_per_step, int* mixed_members)
+{
+    if (!b) return KIN_EINVAL;
+    if (launches_per_step) *launches_per_step = (int)(b->groups.size() + b->solo.size());
+    if (mixed_members) *mixed_members = b->nmixed;
     return KIN_OK;
 }
 
@@ -1409,6 +1487,7 @@ extern "C" kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* mo
     }
     c.want_threads = opts->threads;
     c.want_stages = opts->stages;
+    c.wait_timeout_s = opts->wait_timeout_s;     // the bound on device waits, as in kin_create
     c.cells = 1;
     for (int a = 0; a < 3; ++a) {
         c.adv[a] = model->adv[a];

@@ -102,6 +102,19 @@ struct FixedKernel {
     size_t smem;
 };
 
+// A compiled one-launch kernel for batches of 2D Euler FP32 problems of
+// degrees 1..3 (step_kernel_mixed2d): fn(const Inst*, const int2*, int).
+// block[p - 1] is the cell block a member of degree p must use to join it.
+struct MixedKernel {
+    const void* fn;
+    int threads;
+    int min_blocks;          // resident blocks per SM the kernel is built for
+    size_t smem;
+    int block[3][2];
+};
+// The compiled mixed kernels (at most max of them); returns their count.
+int mixed_kernels_2d(MixedKernel* out, int max);
+
 // Fixed-shape kernel for (degree, system, precision, block) with one or two
 // shared-memory tile buffers, or fn == nullptr.
 FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3], int stages);

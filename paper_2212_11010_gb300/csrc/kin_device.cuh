@@ -317,26 +317,32 @@ __device__ __forceinline__ void lines_axis(const Inst& I, int bx, int by, int bz
 
         if (!SUMMARY) {
             T t = tin[it];
-            T Pm[NP][NP], g[NP];
+            T Pm[NP][NP];
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                g[i] = rec[kOffG + i];
+            for (int i = 0; i < NP; ++i)
 #pragma unroll
                 for (int j = 0; j < NP; ++j) Pm[i][j] = rec[i * NP + j];
-            }
 #pragma unroll 4
             for (int cc = 0; cc < Ba; ++cc) {
                 const int c = sgn == 0 ? cc : Ba - 1 - cc;
                 T* p = line_p + c * cs;
-                T u[NP], dlt[NP];
+                T u[NP], du[NP], dlt[NP];
 #pragma unroll
-                for (int j = 0; j < NP; ++j) u[j] = p[j * ns];
+                for (int j = 0; j < NP; ++j) {
+                    u[j] = p[j * ns];
+                    du[j] = u[j] - t;
+                }
+                // f* - f^n at node i in difference form: (P - I) u + g t
+                // = (P - I)(u - t 1), because (P - I) 1 + g = 0 (A 1 = W 1 +
+                // nu e_in: the derivative of a constant vanishes).  A constant
+                // state then stays exactly constant whatever the rounding of
+                // the coefficients, which removes the systematic FP32 drift.
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    T acc = Pm[i][0] * u[0];
+                    T acc = Pm[i][0] * du[0];
 #pragma unroll
-                    for (int j = 1; j < NP; ++j) acc = fma(Pm[i][j], u[j], acc);
-                    dlt[i] = fma(g[i], t, acc);     // f* - f^n at node i
+                    for (int j = 1; j < NP; ++j) acc = fma(Pm[i][j], du[j], acc);
+                    dlt[i] = acc;
                 }
                 t = sgn == 0 ? u[NP - 1] + dlt[NP - 1] : u[0] + dlt[0];
 #pragma unroll
@@ -401,6 +407,23 @@ __device__ __forceinline__ TileXYZ tile_xyz(const Inst& I, int t)
     return c;
 }
 
+// W / (2d), the equilibrium's isotropic part.  1/(2d) is exact in binary for
+// d = 1, 2.  For d = 3 a product with the rounded 1/6 would carry the same
+// relative error at every node and step: sum_k M_k = 6 base would then
+// differ from W by a fixed factor, and with omega = 2 the moments would
+// drift by 2 x 3e-8 per step in FP32.  The quotient is therefore corrected
+// with its exact residual (one FMA each), which leaves an unbiased rounding.
+template <int D, typename T>
+__device__ __forceinline__ T div2d(T w)
+{
+    if constexpr (D == 3) {
+        const T q = w * T(1.0 / 6.0);
+        return fma(fma(T(-6), q, w), T(1.0 / 6.0), q);
+    } else {
+        return w * T(1.0 / (2.0 * D));
+    }
+}
+
 // Maxwell flux Q(W, e_a) = (-e_a x H, e_a x E) of W = (E, H) (Sec. 6.1.1):
 // with (a, j, k) a cyclic permutation of the axes, e_a x X = (X_j e_k - X_k e_j).
 template <typename V>
@@ -421,7 +444,7 @@ __device__ __forceinline__ void maxwell_flux(const V* W, int a, V* Q, V zero)
 // equilibrium, f <- M(W+) + (1 - omega) (f - M(W-)), on the six axis
 // velocities stored as fk[(2a + s) * 6 + v] (s = 0 for +lambda e_a).
 template <typename T>
-__device__ __forceinline__ void maxwell_relax_node(T* fk, const T* W, T mu, T om1, T inv2d, T inv2l)
+__device__ __forceinline__ void maxwell_relax_node(T* fk, const T* W, T mu, T om1, T inv2l)
 {
     constexpr int M = 6;
     T Wp[M];
@@ -436,8 +459,8 @@ __device__ __forceinline__ void maxwell_relax_node(T* fk, const T* W, T mu, T om
         for (int v = 0; v < M; ++v) {
             // Q^a has no component along E_a and H_a
             const bool z = v == a || v == 3 + a;
-            const T bm = W[v] * inv2d, hm = z ? T(0) : Qm[v] * inv2l;
-            const T bp = Wp[v] * inv2d, hp = z ? T(0) : Qp[v] * inv2l;
+            const T bm = div2d<3>(W[v]), hm = z ? T(0) : Qm[v] * inv2l;
+            const T bp = div2d<3>(Wp[v]), hp = z ? T(0) : Qp[v] * inv2l;
             T& fp = fk[(2 * a) * M + v];
             T& fm = fk[(2 * a + 1) * M + v];
             fp = fma(om1, fp - (z ? bm : bm + hm), z ? bp : bp + hp);
@@ -460,7 +483,6 @@ __device__ __forceinline__ void relax_block(const Inst& I, T* s, int bcells)
     const int pstride = bcells * NN;
     const T omega = T(I.omega);
     const bool two = I.omega == 2.0;
-    const T inv2d = T(1.0 / (2.0 * D));
     const T inv2l = T(1.0 / (2.0 * I.lambda));
     const T gm1 = T(I.gamma - 1.0);
     for (int nd = threadIdx.x; nd < nnodes; nd += blockDim.x) {
@@ -476,7 +498,7 @@ __device__ __forceinline__ void relax_block(const Inst& I, T* s, int bcells)
             W[v] = acc.s;
         }
         if constexpr (SYS == kMaxwell) {
-            maxwell_relax_node(fk, W, T(I.mu), T(1) - omega, inv2d, inv2l);
+            maxwell_relax_node(fk, W, T(I.mu), T(1) - omega, inv2l);
 #pragma unroll
             for (int pp = 0; pp < NPOP; ++pp) s[pp * pstride + nd] = fk[pp];
             continue;
@@ -503,7 +525,7 @@ __device__ __forceinline__ void relax_block(const Inst& I, T* s, int bcells)
             }
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                const T base = W[v] * inv2d;
+                const T base = div2d<D>(W[v]);
                 const T half = Q[v] * inv2l;
                 T& fp = fk[(2 * a) * M + v];
                 T& fm = fk[(2 * a + 1) * M + v];
@@ -683,9 +705,17 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const __grid_constant__ 
         if (tid == 0) flag = mbar_wait_bounded(&bar[st], parity, I.wait_cycles) ? 1 : 0;
         __syncthreads();
         if (flag == 0) {
-            // give up: report, wait (bounded) for the copies still in flight, return
+            // give up: report the error, then wait once more (bounded) for the
+            // bulk loads this block issued into its own shared memory -- the
+            // stalled stage's and, with two stages, the next tile's: a bulk
+            // copy cannot be cancelled, and the block's shared memory must
+            // not be released while one may still write it -- and for the
+            // block's bulk stores (bulk_wait_all); then leave.  A load that
+            // has still not landed after the second bound is beyond repair
+            // here; the error word makes the host poison the context.
             if (tid == 0) {
                 if (I.err) atomicOr(I.err, kErrLoadTimeout);
+                mbar_wait_bounded(&bar[st], parity, I.wait_cycles);
                 if (two && tn < ntiles) mbar_wait_bounded(&bar[st ^ 1], ((i + 1) >> 1) & 1, I.wait_cycles);
             }
             if (warp0) bulk_wait_all();

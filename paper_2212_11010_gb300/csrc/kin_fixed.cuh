@@ -223,15 +223,20 @@ __device__ __forceinline__ void pm_item(const Inst& I, int local, int org0, int 
 #pragma unroll
             for (int cc = 0; cc < BA; ++cc) {
                 T* const p = base + (sg == 0 ? cc : BA - 1 - cc) * CST;
-                T u[NP], dlt[NP];
+                T u[NP], du[NP], dlt[NP];
 #pragma unroll
-                for (int j = 0; j < NP; ++j) u[j] = p[j * NS];
+                for (int j = 0; j < NP; ++j) {
+                    u[j] = p[j * NS];
+                    du[j] = u[j] - t;
+                }
+                // difference form (P - I)(u - t 1) of (P - I) u + g t: exact
+                // for constant states whatever the coefficients' rounding
 #pragma unroll
                 for (int i = 0; i < NP; ++i) {
-                    T acc = cget<BATCH>(I, csm, dir, i * NP) * u[0];
+                    T acc = cget<BATCH>(I, csm, dir, i * NP) * du[0];
 #pragma unroll
-                    for (int j = 1; j < NP; ++j) acc = fma(cget<BATCH>(I, csm, dir, i * NP + j), u[j], acc);
-                    dlt[i] = fma(cget<BATCH>(I, csm, dir, kOffG + i), t, acc);
+                    for (int j = 1; j < NP; ++j) acc = fma(cget<BATCH>(I, csm, dir, i * NP + j), du[j], acc);
+                    dlt[i] = acc;
                 }
                 t = sg == 0 ? u[NP - 1] + dlt[NP - 1] : u[0] + dlt[0];
 #pragma unroll
@@ -307,13 +312,11 @@ __device__ __forceinline__ void pm_group4(const Inst& I, int git, int org0, int 
         return reinterpret_cast<float4*>(slab + off + 4 * j);
     };
     if (MODE == 1) {
-        float Pm[4][4], g[4];
+        float Pm[4][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            g[i] = cget<BATCH>(I, csm, dir, kOffG + i);
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) Pm[i][j] = cget<BATCH>(I, csm, dir, i * 4 + j);
-        }
         const float4 t0 = *tin4;
         float t[4] = {t0.x, t0.y, t0.z, t0.w};
         // the cell loop is unrolled per axis so that every offset is an immediate
@@ -334,13 +337,16 @@ __device__ __forceinline__ void pm_group4(const Inst& I, int git, int org0, int 
             float nw[4][4];
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
-                float dlt[4];
+                float dlt[4], du[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) du[j] = u[l][j] - t[l];
+                // difference form, as in pm_item
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    float acc = Pm[i][0] * u[l][0];
+                    float acc = Pm[i][0] * du[0];
 #pragma unroll
-                    for (int j = 1; j < 4; ++j) acc = fmaf(Pm[i][j], u[l][j], acc);
-                    dlt[i] = fmaf(g[i], t[l], acc);
+                    for (int j = 1; j < 4; ++j) acc = fmaf(Pm[i][j], du[j], acc);
+                    dlt[i] = acc;
                 }
                 t[l] = sg == 0 ? u[l][3] + dlt[3] : u[l][0] + dlt[0];
 #pragma unroll
@@ -555,7 +561,6 @@ __device__ __forceinline__ void fixed_relax(const Inst& I, T* s)
     constexpr int M = S::M, NV = 2 * D, NPOP = S::NPOP;
     const T omega = T(I.omega);
     const bool two = I.omega == 2.0;
-    const T inv2d = T(1.0 / (2.0 * D));
     const T inv2l = T(1.0 / (2.0 * I.lambda));
     const T gm1 = T(I.gamma - 1.0);
 #pragma unroll
@@ -575,7 +580,7 @@ __device__ __forceinline__ void fixed_relax(const Inst& I, T* s)
             W[v] = acc.s;
         }
         if constexpr (SYS == kMaxwell) {
-            maxwell_relax_node(fk, W, T(I.mu), T(1) - omega, inv2d, inv2l);
+            maxwell_relax_node(fk, W, T(I.mu), T(1) - omega, inv2l);
 #pragma unroll
             for (int pp = 0; pp < NPOP; ++pp) s[pp * S::PSTR + o] = fk[pp];
             continue;
@@ -602,7 +607,7 @@ __device__ __forceinline__ void fixed_relax(const Inst& I, T* s)
             }
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                const T base = W[v] * inv2d;
+                const T base = div2d<D>(W[v]);
                 const T half = Q[v] * inv2l;
                 T& fp = fk[(2 * a) * M + v];
                 T& fm = fk[(2 * a + 1) * M + v];
@@ -627,6 +632,17 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// div2d on a node pair
+template <int D>
+__device__ __forceinline__ float2 div2d2(float2 w)
+{
+    if constexpr (D == 3) {
+        const float2 q = __fmul2_rn(w, f2(1.0f / 6.0f));
+        return __ffma2_rn(__ffma2_rn(f2(-6.0f), q, w), f2(1.0f / 6.0f), q);
+    } else {
+        return __fmul2_rn(w, f2((float)(1.0 / (2.0 * D))));
+    }
+}
 
 // The relaxation of fixed_relax on two neighbouring nodes at a time (FP32,
 // rows of even length): the populations of a node pair are one 8-byte
@@ -640,7 +656,6 @@ __device__ __forceinline__ void fixed_relax_pairs(const Inst& I, float* s)
     static_assert(S::ROWLEN % 2 == 0 && S::RSTR % 2 == 0 && S::PSTR % 2 == 0, "node pairs must be 8-byte words");
     const bool two = I.omega == 2.0;
     const float2 om = f2((float)I.omega), omc = f2(1.0f - (float)I.omega);
-    const float2 inv2d = f2((float)(1.0 / (2.0 * D)));
     const float2 inv2l = f2((float)(1.0 / (2.0 * I.lambda)));
     const float2 gm1 = f2((float)(I.gamma - 1.0));
     const float2 twof = f2(2.0f);
@@ -705,7 +720,7 @@ __device__ __forceinline__ void fixed_relax_pairs(const Inst& I, float* s)
 #pragma unroll
                 for (int v = 0; v < M; ++v) {
                     const bool z = v == a || v == 3 + a;
-                    const float2 bm = mul2(W[v], inv2d), bp = mul2(Wp[v], inv2d);
+                    const float2 bm = div2d2<D>(W[v]), bp = div2d2<D>(Wp[v]);
                     const float2 hm = z ? zero : mul2(Qm[v], inv2l), hp = z ? zero : mul2(Qp[v], inv2l);
                     const int ip = (2 * a) * M + v, im = (2 * a + 1) * M + v;
                     const float2 fp = get(ip), fm = get(im);
@@ -739,7 +754,7 @@ __device__ __forceinline__ void fixed_relax_pairs(const Inst& I, float* s)
             }
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                const float2 base = mul2(W[v], inv2d);
+                const float2 base = div2d2<D>(W[v]);
                 const float2 hq = mul2(Q[v], inv2l);
                 const int ip = (2 * a) * M + v, im = (2 * a + 1) * M + v;
                 const float2 fp = get(ip), fm = get(im);
@@ -915,6 +930,64 @@ __global__ void __launch_bounds__(NTH, MINB)
         __syncthreads();
         fixed_compute<D, P, SYS, T, B0, B1, B2, NTH, true>(I, wk.y, cur, tin, nullptr);
         wk = wkn;
+    }
+}
+
+}  // namespace kin
+
+namespace kin {
+
+// ---------------------------------------------------------------------------
+// One launch per step for a batch of 2D Euler problems of different degrees
+// ---------------------------------------------------------------------------
+
+// One tile of a fixed shape with one shared-memory buffer: look-back, load,
+// sweep, relaxation, store, summaries (the one-buffer schedule of
+// step_kernel_fixed), ending at a barrier so that the buffer can be reused.
+template <int D, int P, int SYS, typename T, int B0, int B1, int B2, int NTH>
+__device__ __forceinline__ void fixed_tile_1buf(const Inst& I, int t, T* s, T* tin)
+{
+    if (I.mode == 0) fixed_chain_tile<D, P, SYS, T, B0, B1, B2, NTH>(I, t, tin);
+    fixed_load<D, P, SYS, T, B0, B1, B2, NTH>(I, t, s);
+    cp_wait_all();
+    __syncthreads();
+    fixed_compute<D, P, SYS, T, B0, B1, B2, NTH, true>(I, t, s, tin, nullptr);
+}
+
+// Shared-memory layout of the mixed kernel: one tile buffer as large as the
+// largest of the three shapes (cell blocks X0 x X1 for degree 1, Y0 x Y1 for
+// degree 2, Z0 x Z1 for degree 3; FP32), then the look-back inflows.
+template <int X0, int X1, int Y0, int Y1, int Z0, int Z1>
+struct Mixed2D {
+    using S1 = Shape<2, 1, kEuler, float, X0, X1, 1>;
+    using S2 = Shape<2, 2, kEuler, float, Y0, Y1, 1>;
+    using S3 = Shape<2, 3, kEuler, float, Z0, Z1, 1>;
+    static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
+    static constexpr size_t TILE = (mx(S1::SMEM, mx(S2::SMEM, S3::SMEM)) + 15) / 16 * 16;
+    static constexpr size_t TIN = mx(S1::TIN_BYTES, mx(S2::TIN_BYTES, S3::TIN_BYTES));
+    static constexpr size_t SMEM = TILE + TIN;
+};
+
+// Persistent kernel over a work list of (degree << 24 | instance, tile)
+// pairs covering every tile of every member: each tile runs the fixed-shape
+// body of its degree, so one launch advances problems of degrees 1, 2 and 3
+// (of any mesh size) by one step.  The host orders the list with the most
+// expensive tiles first, so the launch ends on short tiles.
+template <int NTH, int MINB, int X0, int X1, int Y0, int Y1, int Z0, int Z1>
+__global__ void __launch_bounds__(NTH, MINB)
+    step_kernel_mixed2d(const Inst* __restrict__ insts, const int2* __restrict__ work, int nwork)
+{
+    using MX = Mixed2D<X0, X1, Y0, Y1, Z0, Z1>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* const s = reinterpret_cast<float*>(smem_raw);
+    float* const tin = reinterpret_cast<float*>(smem_raw + MX::TILE);
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int2 wk = work[w];
+        const Inst& I = insts[wk.x & 0xffffff];
+        const int deg = wk.x >> 24;
+        if (deg == 1) fixed_tile_1buf<2, 1, kEuler, float, X0, X1, 1, NTH>(I, wk.y, s, tin);
+        else if (deg == 2) fixed_tile_1buf<2, 2, kEuler, float, Y0, Y1, 1, NTH>(I, wk.y, s, tin);
+        else fixed_tile_1buf<2, 3, kEuler, float, Z0, Z1, 1, NTH>(I, wk.y, s, tin);
     }
 }
 

@@ -47,6 +47,35 @@ FixedKernel fixed_kernel_d2(int degree, int system, int prec, const int B[3], in
     return k;
 }
 
+// One-launch kernels for batches of 2D Euler FP32 problems of degrees 1..3:
+// (threads, min blocks per SM, degree-1 block, degree-2 block, degree-3 block).
+// The slots are the default blocks of each degree.  (Smaller blocks at five
+// resident blocks of 192 threads, or four of 256, measured 35-45% slower on
+// the 64-instance mix: the degree-3 sweeps need 80 registers.)
+#define KIN_MIXED_2D(X) X(256, 3, 16, 16, 8, 8, 8, 8)
+
+int mixed_kernels_2d(MixedKernel* out, int max)
+{
+    int n = 0;
+#define KIN_MX(NT, MB, X0, X1, Y0, Y1, Z0, Z1)                                                  \
+    if (n < max) {                                                                              \
+        out[n].fn = (const void*)step_kernel_mixed2d<NT, MB, X0, X1, Y0, Y1, Z0, Z1>;             \
+        out[n].threads = NT;                                                                    \
+        out[n].min_blocks = MB;                                                                 \
+        out[n].smem = Mixed2D<X0, X1, Y0, Y1, Z0, Z1>::SMEM;                                    \
+        out[n].block[0][0] = X0;                                                                \
+        out[n].block[0][1] = X1;                                                                \
+        out[n].block[1][0] = Y0;                                                                \
+        out[n].block[1][1] = Y1;                                                                \
+        out[n].block[2][0] = Z0;                                                                \
+        out[n].block[2][1] = Z1;                                                                \
+        ++n;                                                                                    \
+    }
+    KIN_MIXED_2D(KIN_MX)
+#undef KIN_MX
+    return n;
+}
+
 StepKernel step_kernel_d2(int degree, int system, int prec)
 {
     switch (degree * 4 + system) {        // (Maxwell is 3D only)

@@ -43,8 +43,14 @@ def state_bytes_estimate(w, esize=4) -> int:
 
 class Server:
     def __init__(self, budget_bytes: float = 150e9, chunk_steps: int = 25, torch_alloc: bool = True,
-                 keep_results: bool = True, pinned_results: bool = True):
+                 keep_results: bool = True, pinned_results: bool = True, mixed=None):
         self.budget = float(budget_bytes)
+        # batch schedule: the autotuner's choice for this GPU unless given
+        # (membership changes every few chunks, too often to tune each batch)
+        if mixed is None:
+            from .autotune import batch_choice
+            mixed = batch_choice().mixed
+        self.mixed = bool(mixed)
         self.chunk = int(chunk_steps)
         self.torch_alloc = torch_alloc
         self.keep_results = keep_results
@@ -93,6 +99,7 @@ class Server:
         run_stream = torch.cuda.Stream()
         adm_stream = torch.cuda.Stream()
         chunks = []            # (start, end) events of every chunk on the run stream
+        self.peak_bytes = 0    # most device bytes held by admitted requests at once
         t0 = clock()
 
         def admit(now):
@@ -113,6 +120,7 @@ class Server:
                 rec.steps = r.steps
                 rec.dofs = w.kinetic_dofs
                 used += ctx.info.device_bytes
+                self.peak_bytes = max(self.peak_bytes, used)
                 new.append([rec, ctx, r.steps, ctx.info.device_bytes])
             return new
 
@@ -121,7 +129,8 @@ class Server:
             if active:
                 if batch is None:
                     # membership changes every few chunks: direct launches, no graph capture
-                    batch = Batch([a[1] for a in active], stream=run_stream.cuda_stream, graphs=False)
+                    batch = Batch([a[1] for a in active], stream=run_stream.cuda_stream, graphs=False,
+                                  mixed=self.mixed)
                 k = min(self.chunk, min(a[2] for a in active))
                 ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 ev[0].record(run_stream)

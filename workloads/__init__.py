@@ -323,18 +323,26 @@ class Request:
 
 
 def serving_stream(seed: int = 0, count: int = 64, rate: float = 200.0, sizes=(64, 128, 256, 512, 1024),
-                   degrees=(1, 2, 3), steps=(50, 500)):
+                   degrees=(1, 2, 3), steps=(50, 500), size_range=None, size_step: int = 32):
     """Poisson arrivals (mean 'rate' per second) of 2D Euler / D2Q4 requests:
-    mesh n x n with n log-uniform over the powers of two in [64, 1024]
-    (uniform over the exponents), DG degree uniform in 'degrees', step count
-    uniform in [steps[0], steps[1]], vortex or density wave 50/50."""
+    DG degree uniform in 'degrees', step count uniform in [steps[0],
+    steps[1]], vortex or density wave 50/50.  Mesh n x n: with size_range =
+    (lo, hi), n is log-uniform on [lo, hi] rounded to a multiple of size_step
+    (the 32-cell subdomain extent) -- the serving configuration's
+    64^2..1024^2; otherwise n is uniform over the list 'sizes'."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     for i in range(count):
         t += float(rng.exponential(1.0 / rate))
-        out.append(Request(i, t, "vortex" if rng.uniform() < 0.5 else "densitywave",
-                           int(rng.choice(sizes)), int(rng.choice(degrees)),
+        kind = "vortex" if rng.uniform() < 0.5 else "densitywave"
+        if size_range is not None:
+            lo, hi = size_range
+            n = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+            n = int(min(hi, max(lo, size_step * round(n / size_step))))
+        else:
+            n = int(rng.choice(sizes))
+        out.append(Request(i, t, kind, n, int(rng.choice(degrees)),
                            int(rng.integers(steps[0], steps[1] + 1)), int(rng.integers(0, 8))))
     return out
 
