@@ -205,7 +205,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "50"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -233,11 +233,13 @@ class ClockSampler:
                 self.proc.kill()
             self.thread.join(timeout=2)
 
+    MARGIN_S = 0.1     # samples this close to the timed window count (the region can be ~40 ms)
+
     def summary(self):
         rows = self.rows
         if self.window is not None:
             a, b = self.window
-            inside = [r for t, r in rows if a <= t <= b + 0.06]
+            inside = [r for t, r in rows if a - self.MARGIN_S <= t <= b + self.MARGIN_S]
             rows = inside
         else:
             rows = [r for _, r in rows]
@@ -254,7 +256,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self_rows)}
+                "reasons": sorted(reasons), "samples": len(self_rows),
+                "window_margin_s": self.MARGIN_S, "interval_ms": 20}
 
 
 def measured_peak_hbm():
@@ -531,7 +534,7 @@ def run_batched(args):
     import paper_2212_11010_gb300 as kin
     from paper_2212_11010_gb300 import autotune
     ws, rank, dev = _setup_gpu()
-    mix = workloads.batched_mix(seed=0, count=64)
+    mix = workloads.batched_mix(seed=0, count=args.instances)
     dofs = sum(w.kinetic_dofs for w in mix)
     stream = torch.cuda.Stream()
     ctxs = []
@@ -639,8 +642,11 @@ def run_batched(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": BATCHED_DESC, "instances": len(mix), "kinetic_dofs": dofs,
-                   "state_bytes": 4 * dofs, "l2": "state 4.4 GB exceeds L2 (129 MB); no flush",
+        "config": {"workload": BATCHED_DESC if args.instances == 64 else
+                   BATCHED_DESC.replace("64x", f"{args.instances}x"), "instances": len(mix), "kinetic_dofs": dofs,
+                   "state_bytes": 4 * dofs,
+                   "l2": f"state {4 * dofs / 1e9:.1f} GB exceeds L2 (129 MB); no flush"
+                         if 4 * dofs > 1e9 else "state comparable to L2: not for roofline figures",
                    "launches_per_step": launches, "schedule": sched.label,
                    "schedule_ms_per_step": {s_.label: v for s_, v in sched_ms.items()},
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu"},
@@ -852,6 +858,8 @@ def main():
                              "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d", "vortex2d-512-p3",
                              "maxwell3d-dirichlet"])
     ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--instances", type=int, default=64,
+                    help="instances of the batched mix (64 is the configuration; fewer for small profiler captures)")
     ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")

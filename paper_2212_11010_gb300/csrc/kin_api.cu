@@ -255,6 +255,15 @@ static Inst make_inst(const kin_ctx* c, int mode)
     I.mu = c->system == KIN_MAXWELL ? (1.0 - 0.5 * c->sigma * c->dt) / (1.0 + 0.5 * c->sigma * c->dt) : 1.0;
     for (int a = 0; a < 3; ++a) I.inflow[a] = c->inflow[a];
     I.bnd = c->bnd_dev;
+    // look-back depth per direction: the fewest upstream blocks d with
+    // |rho^B|^d <= tol, tol well below the rounding of the precision
+    const double tol = c->esize == 4 ? std::ldexp(1.0, -36) : std::ldexp(1.0, -72);
+    for (int d = 0; d < 6; ++d) {
+        const double rb = std::fabs(c->coef_host[d][kOffRhoB]);
+        int depth = 1 << 30;                                   // no truncation
+        if (rb < 1.0) depth = rb == 0.0 ? 1 : std::max(1, (int)std::ceil(std::log(tol) / std::log(rb)));
+        I.lbdepth[d] = depth;
+    }
     return I;
 }
 

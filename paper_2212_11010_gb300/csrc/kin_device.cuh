@@ -103,6 +103,12 @@ struct __align__(16) Inst {
     double lambda, gamma, omega;
     double mu;               // Maxwell: conductivity source factor (1 - sigma dt/2) / (1 + sigma dt/2)
     int inflow[3];           // 1: axis a has inflow boundaries instead of being periodic
+    // look-back depth per (axis, sign): only the last lbdepth blocks of a walk
+    // are folded; every earlier contribution reaches the inflow damped by
+    // rho^B per block, i.e. by at most rho^(B lbdepth), which the host keeps
+    // below 2^-36 (FP32) or 2^-72 (FP64) -- far below the rounding of the
+    // result, so the truncated walk returns the same inflow up to rounding
+    int lbdepth[6];
     // T*: inflow boundaries: per population the value across the
     // domain-boundary face it enters through, M_k(W_b)[v] of that face's state
     const void* bnd;
@@ -148,22 +154,30 @@ __device__ __forceinline__ T chain_inflow(const Inst& I, int a, int sgn, int bid
     const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)pop * I.raw_stride + gline;
     const T RB = coef_of(I, 2 * a + sgn, kOffRhoB, T(0));
     int s0 = S - K;
-    T t;
-    int cnt;
-    const T* p;
-    if (I.inflow[a] && s0 < 0) {
+    int cnt, q0;
+    const bool from_bnd = I.inflow[a] && s0 < 0;
+    if (from_bnd) {
         // the walk reaches the domain boundary within K subdomains: it starts
         // there from the boundary value (the same in every iteration) and
         // folds every block from the first one
-        t = bnd_of<T>(I, pop);
         cnt = S * nb + r;
-        p = sig;
+        q0 = 0;
     } else {
         while (s0 < 0) s0 += NS;
-        t = __ldg(raw + (long long)s0 * gl);
         cnt = (K - 1) * nb + r;
-        p = sig + (long long)((s0 + 1 == NS) ? 0 : (s0 + 1) * nb) * gl;
+        q0 = (s0 + 1 == NS) ? 0 : (s0 + 1) * nb;
     }
+    T t;
+    const int depth = I.lbdepth[2 * a + sgn];
+    if (cnt > depth) {
+        // only the last 'depth' blocks matter (see Inst::lbdepth)
+        q0 = (q0 + cnt - depth) % nbk;
+        cnt = depth;
+        t = T(0);
+    } else {
+        t = from_bnd ? bnd_of<T>(I, pop) : __ldg(raw + (long long)s0 * gl);
+    }
+    const T* p = sig + (long long)q0 * gl;
     // walk the summaries of blocks q0, q0+1, ... (periodic) by pointer stride
     const T* const end = sig + (long long)nbk * gl;
 #pragma unroll 4

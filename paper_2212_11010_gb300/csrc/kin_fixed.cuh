@@ -467,6 +467,14 @@ __device__ __forceinline__ void chain_setup(const Inst& I, int hid, int sgn, int
     const long long gl = I.ax[A].glines;
     cnt = from_bnd ? Sd * nbs + r : (K - 1) * nbs + r;
     qj = from_bnd ? 0 : ((s0 + 1 == NSa) ? 0 : (s0 + 1) * nbs);
+    // only the last lbdepth blocks of the walk matter (see Inst::lbdepth):
+    // a longer walk starts that many blocks upstream from a zero inflow
+    const int depth = I.lbdepth[2 * A + sgn];
+    const bool trunc = cnt > depth;
+    if (trunc) {
+        qj = (qj + cnt - depth) % nbk;
+        cnt = depth;
+    }
     RB = coef_of(I, 2 * A + sgn, kOffRhoB, T(0));
     const T* __restrict__ raw = static_cast<const T*>(I.raw_in) + (long long)s0 * gl;
 #pragma unroll
@@ -481,7 +489,9 @@ __device__ __forceinline__ void chain_setup(const Inst& I, int hid, int sgn, int
         const long long gline = fixed_gline<D, NP, A, B0, B1>(I, line, org0, org1, org2);
         const int pop = (2 * A + sgn) * M + v;
         off[k] = (int)((long long)pop * I.sig_stride + gline);   // fits: checked on the host
-        tr[k] = __ldg(from_bnd ? static_cast<const T*>(I.bnd) + pop : raw + (long long)pop * I.raw_stride + gline);
+        tr[k] = trunc ? T(0)
+                      : __ldg(from_bnd ? static_cast<const T*>(I.bnd) + pop
+                                       : raw + (long long)pop * I.raw_stride + gline);
     }
 }
 

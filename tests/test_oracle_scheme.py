@@ -72,6 +72,21 @@ def test_isentropic_vortex_converges():
     assert np.all(_orders(errs) > 1.4), errs
 
 
+def test_isentropic_vortex_time_order_two():
+    # dt refinement against the vortex's closed form (the free stream carries
+    # it undeformed): omega = 2 is second order in time (Sec. 2.2 remark,
+    # Sec. 2.4).  The box is 20 wide so that the vortex's tail at the periodic
+    # boundary (~exp((1 - 100)/2)) is far below every error, and degree 3 on
+    # 64^2 cells keeps the spatial error below the smallest temporal one; the
+    # steps are 6.5x down to 1.6x the explicit DG limit.
+    errs = []
+    for dt in (0.06, 0.03, 0.015):
+        w = workloads.with_(workloads.vortex2d(seed=0, n=64, degree=3, tiles=2, box=20.0), dt=dt)
+        W, t = _run(w, T=0.6)
+        errs.append(np.abs(W - w.exact(t)).max())
+    assert np.all(np.abs(_orders(errs) - 2.0) < 0.15), errs
+
+
 def test_advection_1d_config_one_vs_four_subdomains():
     # 256 cells, p = 1, lambda = 2, dt = 4h/lambda, 100 steps: the interface
     # coupling decays like (8/13)^64 per subdomain, far below round-off.
