@@ -85,19 +85,29 @@ def flops_per_dof(dim, degree, m, nvel, maxwell=False):
 # only while the sources are unchanged, else the line's traffic is null.
 # Keys: (workload, precision); the batched figure is per batch step (all its
 # launches), scaled from a capture of a smaller mix by the kinetic DOF.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # 64-instance batched mix, one step = three launches (degree 2, 1, 3):
+    # read 674.2 + 497.6 + 3411 MB, write 619.9 + 439.8 + 3361 MB
+    ("batched", "f32"): (9.0035e9, "eed7a2e564c5b11d"),
+}
+# the same capture per launch, keyed by degree
+NCU_TRAFFIC_PER_DEGREE = {1: (0.9374e9, "eed7a2e564c5b11d"), 2: (1.2941e9, "eed7a2e564c5b11d"),
+                          3: (6.772e9, "eed7a2e564c5b11d")}
+
+
+# device sources of the axis-velocity step kernels (single, batched, mixed)
+STEP_KERNEL_SOURCES = ("kin_device.cuh", "kin_fixed.cuh", "kin_tma.cuh", "kin_step_d1.cu", "kin_step_d2.cu",
+                       "kin_step_d3.cu")
 
 
 def source_hash():
-    """sha256 (16 hex digits) of the CUDA sources and the public header."""
+    """sha256 (16 hex digits) of the step kernels' device sources."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2212_11010_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in STEP_KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode() + b"\0" + fh.read())
-    with open(os.path.join(ROOT, "include", "kin.h"), "rb") as fh:
-        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -544,8 +554,13 @@ def run_batched(args):
         ctxs.append(c)
     steps_done = [0] * len(mix)
 
-    # schedule: the autotuner times the candidate batch schedules on these members (untimed)
-    sched, sched_ms, taken = autotune.tune_batch(ctxs, stream)
+    # schedule: the autotuner times the candidate batch schedules on these
+    # members (untimed); --schedule fixes it instead (profiler runs, where
+    # serialised launches would skew the tuner's timings)
+    if args.schedule == "auto":
+        sched, sched_ms, taken = autotune.tune_batch(ctxs, stream)
+    else:
+        sched, sched_ms, taken = autotune.BatchSchedule(args.schedule == "mixed"), {}, 0
     steps_done = [s + taken for s in steps_done]
     batch = kin.Batch(ctxs, stream=stream.cuda_stream, mixed=sched.mixed)
     batch.step(args.warmup)
@@ -585,9 +600,11 @@ def run_batched(args):
     peak, peak_kind = measured_peak_hbm()
     algo_bytes = ALGO_BYTES_PER_DOF["f32"] * dofs
     achieved = algo_bytes / (ms_per_step * 1e-3) / 1e9
-    traffic, traffic_note = traffic_for(("batched", "f32"))
-    for k in per_kernel:
+    traffic, traffic_note = traffic_for(("batched", "f32")) if args.instances == 64 else (None, "not the 64-instance mix")
+    for k, p in zip(per_kernel, sorted({w.degree for w in mix})):
         k["frac"] = k["GBs"] / peak
+        rec = NCU_TRAFFIC_PER_DEGREE.get(p)
+        k["traffic"] = rec[0] if rec and rec[1] == source_hash() and args.instances == 64 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
             "kernel": f"the batch step: {launches} launch(es) of the fused step kernel ({sched.label}), "
@@ -858,6 +875,8 @@ def main():
                              "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d", "vortex2d-512-p3",
                              "maxwell3d-dirichlet"])
     ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--schedule", default="auto", choices=["auto", "per-type", "mixed"],
+                    help="batch schedule: chosen by the autotuner (auto) or fixed")
     ap.add_argument("--instances", type=int, default=64,
                     help="instances of the batched mix (64 is the configuration; fewer for small profiler captures)")
     ap.add_argument("--precision", default=None, choices=[None, "f32", "f64"])
