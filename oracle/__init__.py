@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kin_oracle.c")
+_SRC_TET = os.path.join(_HERE, "kin_oracle_tet.c")
 _HDR = os.path.join(_HERE, "kin_oracle.h")
 _LIB = os.path.join(_HERE, "libkin_oracle.so")
 
@@ -43,10 +44,10 @@ def build(force: bool = False) -> str:
     if override:
         return override
     stale = (not os.path.exists(_LIB)) or any(
-        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _SRC_TET, _HDR))
     if force or stale:
         tmp = _LIB + ".%d.tmp" % os.getpid()
-        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, _SRC_TET, "-o", tmp, "-lm"]
         try:
             subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
         except subprocess.CalledProcessError:
@@ -77,6 +78,18 @@ class _Problem(ctypes.Structure):
     ]
 
 
+class _TetMesh(ctypes.Structure):
+    _fields_ = [
+        ("ncells", ctypes.c_int),
+        ("xyz", ctypes.POINTER(ctypes.c_double)),
+        ("vid", ctypes.POINTER(ctypes.c_longlong)),
+        ("nbr", ctypes.POINTER(ctypes.c_longlong)),
+        ("sub", ctypes.POINTER(ctypes.c_int)),
+        ("nsub", ctypes.c_int),
+        ("wrap", ctypes.POINTER(ctypes.c_int)),
+    ]
+
+
 _lib = None
 
 
@@ -87,6 +100,7 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         pp = ctypes.POINTER(_Problem)
         ip = ctypes.POINTER(ctypes.c_int)
+        tp = ctypes.POINTER(_TetMesh)
         sig = {
             "ko_num_vars": ([pp], ctypes.c_int),
             "ko_num_vel": ([pp], ctypes.c_int),
@@ -105,6 +119,14 @@ def lib():
             "ko_step": ([pp, dp, ctypes.c_int], ctypes.c_int),
             "ko_mass": ([pp, dp, dp], ctypes.c_int),
             "ko_set_threads": ([ctypes.c_int], ctypes.c_int),
+            "ko_init_n": ([pp, dp, dp, ctypes.c_size_t], ctypes.c_int),
+            "ko_moments_n": ([pp, dp, dp, ctypes.c_size_t], ctypes.c_int),
+            "ko_relax_n": ([pp, dp, ctypes.c_size_t], ctypes.c_int),
+            "ko_tet_cell_matrix": ([pp, tp, ctypes.c_int, ctypes.c_int, dp, dp, dp], ctypes.c_int),
+            "ko_tet_transport": ([pp, tp, dp, dp, ip], ctypes.c_int),
+            "ko_tet_step": ([pp, tp, dp, ctypes.c_int], ctypes.c_int),
+            "ko_tet_mass": ([pp, tp, dp, dp], ctypes.c_int),
+            "ko_tet_order": ([pp, tp, ctypes.c_int, ctypes.c_int, ip, ip], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(_lib, name)
@@ -279,3 +301,101 @@ def set_threads(n: int = 0) -> int:
     """Threads of the oracle's parallel loops (n <= 0: unchanged); returns
     the count in use (1 when built without OpenMP)."""
     return int(lib().ko_set_threads(int(n)))
+
+
+# ---------------------------------------------------------------------------
+# tetrahedral meshes
+# ---------------------------------------------------------------------------
+
+class TetMesh:
+    """ko_tetmesh over numpy arrays (kept alive here): xyz (cells, 4, 3),
+    vid (cells, 4), nbr (cells, 4), sub (cells,) subdomain ids, wrap
+    (cells, 4) periodic-boundary faces."""
+
+    def __init__(self, xyz, vid, nbr, sub, wrap):
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self.vid = np.ascontiguousarray(vid, dtype=np.int64)
+        self.nbr = np.ascontiguousarray(nbr, dtype=np.int64)
+        self.sub = np.ascontiguousarray(sub, dtype=np.int32)
+        self.wrap = np.ascontiguousarray(wrap, dtype=np.int32)
+        self.ncells = self.vid.shape[0]
+        self.nsub = int(self.sub.max()) + 1
+        self._c = _TetMesh(self.ncells, self.xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           self.vid.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                           self.nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                           self.sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), self.nsub,
+                           self.wrap.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+
+    @classmethod
+    def from_workload(cls, w):
+        return cls(w.mesh.xyz, w.mesh.vid, w.mesh.nbr, w.subdomains(), w.mesh.wrap)
+
+    @property
+    def nodes(self) -> int:
+        return 4 * self.ncells
+
+
+def tet_problem(w) -> Problem:
+    """The ko_problem of a tetrahedral workload (its kinetic model, dt, K)."""
+    return Problem(dim=3, n=(1, 1, 1), lo=(0, 0, 0), hi=(1, 1, 1), degree=1, system=w.system, lam=w.lam,
+                   dt=w.dt, omega=w.omega, gamma=w.gamma, adv=w.adv, tiles=(1, 1, 1), iters=w.iters,
+                   velset=w.velset, sigma=w.sigma)
+
+
+def tet_init(P: Problem, T: TetMesh, W0) -> np.ndarray:
+    W0 = np.ascontiguousarray(W0, dtype=np.float64).reshape(-1)
+    assert W0.size == P.m * T.nodes
+    f = np.zeros(P.npop * T.nodes)
+    _check(lib().ko_init_n(ctypes.byref(P.c()), _dp(W0), _dp(f), T.nodes), "tet init")
+    return f
+
+
+def tet_moments(P: Problem, T: TetMesh, f: np.ndarray) -> np.ndarray:
+    W = np.zeros(P.m * T.nodes)
+    _check(lib().ko_moments_n(ctypes.byref(P.c()), _dp(f), _dp(W), T.nodes), "tet moments")
+    return W
+
+
+def tet_relax(P: Problem, T: TetMesh, f: np.ndarray) -> None:
+    _check(lib().ko_relax_n(ctypes.byref(P.c()), _dp(f), T.nodes), "tet relax")
+
+
+def tet_transport(P: Problem, T: TetMesh, f: np.ndarray):
+    defect = np.zeros(P.m)
+    it = ctypes.c_int(0)
+    _check(lib().ko_tet_transport(ctypes.byref(P.c()), ctypes.byref(T._c), _dp(f), _dp(defect),
+                                  ctypes.byref(it)), "tet transport")
+    return defect, it.value
+
+
+def tet_step(P: Problem, T: TetMesh, f: np.ndarray, nsteps: int = 1) -> None:
+    _check(lib().ko_tet_step(ctypes.byref(P.c()), ctypes.byref(T._c), _dp(f), nsteps), "tet step")
+
+
+def tet_mass(P: Problem, T: TetMesh, W: np.ndarray) -> np.ndarray:
+    out = np.zeros(P.m)
+    _check(lib().ko_tet_mass(ctypes.byref(P.c()), ctypes.byref(T._c), _dp(np.ascontiguousarray(W)),
+                             _dp(out)), "tet mass")
+    return out
+
+
+def tet_cell_matrix(P: Problem, T: TetMesh, c: int, k: int):
+    """(A, M, V.N_a |F_a| per face) of cell c and velocity k."""
+    A = np.zeros(16)
+    M = np.zeros(16)
+    vna = np.zeros(4)
+    _check(lib().ko_tet_cell_matrix(ctypes.byref(P.c()), ctypes.byref(T._c), c, k, _dp(A), _dp(M), _dp(vna)),
+           "tet cell matrix")
+    return A.reshape(4, 4), M.reshape(4, 4), vna
+
+
+def tet_order(P: Problem, T: TetMesh, k: int, s: int):
+    """(cells in breadth-first topological order, their levels) of subdomain s."""
+    order = np.zeros(T.ncells, dtype=np.int32)
+    level = np.zeros(T.ncells, dtype=np.int32)
+    n = lib().ko_tet_order(ctypes.byref(P.c()), ctypes.byref(T._c), k, s,
+                           order.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                           level.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if n < 0:
+        raise ValueError(f"oracle tet order failed with code {n}")
+    return order[:n].copy(), level[:n].copy()

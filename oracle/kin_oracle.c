@@ -696,8 +696,13 @@ int ko_transport(const ko_problem* P, double* f, double* defect, int* iters_done
 int ko_moments(const ko_problem* P, const double* f, double* W)
 {
     if (check_problem(P) || !f || !W) return -1;
+    return ko_moments_n(P, f, W, ko_num_nodes(P));
+}
+
+int ko_moments_n(const ko_problem* P, const double* f, double* W, size_t nodes)
+{
+    if (check_problem(P) || !f || !W) return -1;
     int m = ko_num_vars(P), nv = ko_num_vel(P);
-    size_t nodes = ko_num_nodes(P);
     for (int v = 0; v < m; ++v) {
 #pragma omp parallel for schedule(static)
         for (size_t i = 0; i < nodes; ++i) {
@@ -712,8 +717,13 @@ int ko_moments(const ko_problem* P, const double* f, double* W)
 int ko_relax(const ko_problem* P, double* f)
 {
     if (check_problem(P) || !f) return -1;
+    return ko_relax_n(P, f, ko_num_nodes(P));
+}
+
+int ko_relax_n(const ko_problem* P, double* f, size_t nodes)
+{
+    if (check_problem(P) || !f) return -1;
     int m = ko_num_vars(P), nv = ko_num_vel(P);
-    size_t nodes = ko_num_nodes(P);
 #pragma omp parallel for schedule(static)
     for (size_t i = 0; i < nodes; ++i) {
         double W[8], M[64];
@@ -747,8 +757,13 @@ int ko_relax(const ko_problem* P, double* f)
 int ko_init(const ko_problem* P, const double* W0, double* f)
 {
     if (check_problem(P) || !W0 || !f) return -1;
+    return ko_init_n(P, W0, f, ko_num_nodes(P));
+}
+
+int ko_init_n(const ko_problem* P, const double* W0, double* f, size_t nodes)
+{
+    if (check_problem(P) || !W0 || !f) return -1;
     int m = ko_num_vars(P), nv = ko_num_vel(P);
-    size_t nodes = ko_num_nodes(P);
 #pragma omp parallel for schedule(static)
     for (size_t i = 0; i < nodes; ++i) {
         double W[8], M[64];

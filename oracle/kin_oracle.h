@@ -90,6 +90,11 @@ int ko_cell_matrix(const ko_problem* P, int k, double* A);
 int ko_init(const ko_problem* P, const double* W0, double* f);
 /* W = sum_k f_k (Sec. 2.2, step 3). */
 int ko_moments(const ko_problem* P, const double* f, double* W);
+/* The same three pointwise steps on 'nodes' nodes of any mesh (the
+ * tetrahedral meshes below): storage W[v][node], f[pop][node]. */
+int ko_init_n(const ko_problem* P, const double* W0, double* f, size_t nodes);
+int ko_moments_n(const ko_problem* P, const double* f, double* W, size_t nodes);
+int ko_relax_n(const ko_problem* P, double* f, size_t nodes);
 /* Crank-Nicolson DG transport of every population over dt, solved by the
  * downwind sweep inside each subdomain with the lagged subdomain coupling of
  * eq. ibvp.  If defect != NULL it receives, per variable, the mass change
@@ -111,6 +116,50 @@ int ko_mass(const ko_problem* P, const double* W, double* mass);
  * unchanged.  Returns the count now in use (1 without OpenMP).  Results do
  * not depend on it. */
 int ko_set_threads(int nthreads);
+
+/* ---- tetrahedral meshes (Sec. 3.1: tetrahedral cells, n_f = 4 faces) ----
+ * P1 nodal basis: the four vertices of each cell (Lagrange functions,
+ * exact integration of the mass, stiffness and face matrices).  Storage:
+ * f[pop][cell][a] with a the cell's local vertex.  Face a of a cell is the
+ * face opposite its vertex a.  Only the kinetic model (system, velset,
+ * lambda, gamma, adv, sigma, omega), dt and iters of the ko_problem are
+ * used, with dim = 3; the mesh and its subdomains come from ko_tetmesh.
+ * Periodic meshes only (every face has a neighbour).  A face is a subdomain
+ * interface (eq. ibvp: inflow from the previous iterate) when the cell across
+ * it lies in another subdomain or when it crosses the periodic boundary (a
+ * subdomain that wraps around the box couples to itself there, as on the
+ * Cartesian meshes; the oriented graph inside a subdomain is then acyclic). */
+typedef struct {
+    int ncells;
+    const double* xyz;  /* [cell][4][3] vertex coordinates (one geometric tetrahedron per cell) */
+    const long long* vid;  /* [cell][4] global vertex ids (matching nodes across faces)   */
+    const long long* nbr;  /* [cell][4] the cell across face a                            */
+    const int* sub;     /* [cell] subdomain id, 0..nsub-1 (Sec. 5.1)                       */
+    int nsub;
+    const int* wrap;    /* [cell][4] 1: face a crosses the periodic boundary of the box    */
+} ko_tetmesh;
+
+/* Local matrices of cell c and velocity k for the implicit half step
+ * tau = dt/2 of eq. dg_imp: A = M + tau (-K + sum_{outflow faces}
+ * (V.N) F_face) (4 x 4, row-major), the mass matrix M (4 x 4), and per face
+ * a the flux V.N_a |F_a| (so the caller sees the orientation). */
+int ko_tet_cell_matrix(const ko_problem* P, const ko_tetmesh* T, int c, int k, double* A, double* M,
+                       double* vn_area);
+/* Crank-Nicolson transport of every population, cells visited in the
+ * topological order of the oriented cell graph of each subdomain (Sec. 3.2,
+ * breadth-first), subdomains coupled by eq. ibvp with P->iters iterations
+ * (0: to the fixed point).  defect (m doubles or NULL): the interface mass
+ * defect of the finite iteration. */
+int ko_tet_transport(const ko_problem* P, const ko_tetmesh* T, double* f, double* defect, int* iters_done);
+/* nsteps applications of relaxation o transport. */
+int ko_tet_step(const ko_problem* P, const ko_tetmesh* T, double* f, int nsteps);
+/* Mass per variable: sum over cells of |L|/4 times the sum of W over the
+ * cell's nodes (the exact integral of the P1 function). */
+int ko_tet_mass(const ko_problem* P, const ko_tetmesh* T, const double* W, double* mass);
+/* Breadth-first topological order of the cells of subdomain s for velocity
+ * k (Sec. 3.2): order receives the cell ids, level their BFS level (the
+ * wavefront: cells of one level are independent).  Returns the count. */
+int ko_tet_order(const ko_problem* P, const ko_tetmesh* T, int k, int s, int* order, int* level);
 
 #ifdef __cplusplus
 }

@@ -61,20 +61,55 @@ PIN_FILES = ["tests/test_oracle_basis.py", "tests/test_oracle_relaxation.py",
              "tests/test_oracle_transport.py", "tests/test_oracle_simplex.py",
              "tests/test_oracle_maxwell.py", "tests/test_oracle_inflow.py"]
 
+# the tetrahedral-mesh transport (kin_oracle_tet.c), pinned by test_oracle_tet.py
+SRC_TET = os.path.join(ROOT, "oracle", "kin_oracle_tet.c")
+MUTATIONS_TET = {
+    "tet_volume_term_sign": ("A[i * 4 + j] = mij - tau * vg * g.vol / 4.0;",
+                             "A[i * 4 + j] = mij + tau * vg * g.vol / 4.0;"),
+    "tet_mass_matrix_lumped": ("const double mij = g.vol / 20.0 * (i == j ? 2.0 : 1.0);",
+                               "const double mij = g.vol / 20.0 * (i == j ? 5.0 : 0.0);"),
+    "tet_outflow_face_mass_diagonal": ("A[i * 4 + j] += tau * vn * g.area[a] / 12.0 * (i == j ? 2.0 : 1.0);",
+                                       "A[i * 4 + j] += tau * vn * g.area[a] / 12.0 * (i == j ? 1.0 : 1.0);"),
+    "tet_interface_uses_current_iterate": ("const double* src = is_interface(T, c, a) ? prev : cur;",
+                                           "const double* src = cur;"),
+    "tet_inflow_node_not_matched": ("fr[j] = src[(size_t)R * 4 + C->match[((size_t)c * 4 + a) * 4 + j]];",
+                                    "fr[j] = src[(size_t)R * 4 + j];"),
+    "tet_normal_points_inward": ("const double s = dot3(n, to_a) > 0 ? -1.0 : 1.0;",
+                                 "const double s = dot3(n, to_a) > 0 ? 1.0 : -1.0;"),
+}
+
+
+def _run_pins(tmp_path, mutated_name, mutated_text, pin_files):
+    """Build the oracle with one source replaced by mutated_text and run the
+    pins against it; returns pytest's exit code."""
+    hdr = os.path.join(ROOT, "oracle", "kin_oracle.h")
+    (tmp_path / "kin_oracle.h").write_text(open(hdr).read())
+    srcs = []
+    for path in (SRC, SRC_TET):
+        dst = tmp_path / os.path.basename(path)
+        dst.write_text(mutated_text if os.path.basename(path) == mutated_name else open(path).read())
+        srcs.append(str(dst))
+    lib = tmp_path / "libkin_oracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *srcs, "-o", str(lib), "-lm"])
+    env = dict(os.environ, KIN_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"]
+                       + pin_files, cwd=ROOT, env=env, capture_output=True, text=True)
+    return r
+
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(name, tmp_path):
     before, after = MUTATIONS[name]
     src = open(SRC).read()
     assert src.count(before) >= 1, "mutation anchor vanished from the oracle source"
-    mutated = tmp_path / "kin_oracle.c"
-    mutated.write_text(src.replace(before, after, 1))
-    hdr = os.path.join(ROOT, "oracle", "kin_oracle.h")
-    (tmp_path / "kin_oracle.h").write_text(open(hdr).read())
-    lib = tmp_path / "libkin_oracle_mut.so"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", str(mutated),
-                           "-o", str(lib), "-lm"])
-    env = dict(os.environ, KIN_ORACLE_LIB=str(lib))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider"]
-                       + PIN_FILES, cwd=ROOT, env=env, capture_output=True, text=True)
+    r = _run_pins(tmp_path, "kin_oracle.c", src.replace(before, after, 1), PIN_FILES)
+    assert r.returncode == 1, f"planted mistake '{name}' passed every pin:\n{r.stdout[-800:]}"
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_TET))
+def test_tet_pins_catch_planted_mistake(name, tmp_path):
+    before, after = MUTATIONS_TET[name]
+    src = open(SRC_TET).read()
+    assert src.count(before) >= 1, "mutation anchor vanished from the tetrahedral oracle source"
+    r = _run_pins(tmp_path, "kin_oracle_tet.c", src.replace(before, after, 1), ["tests/test_oracle_tet.py"])
     assert r.returncode == 1, f"planted mistake '{name}' passed every pin:\n{r.stdout[-800:]}"

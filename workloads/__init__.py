@@ -366,3 +366,213 @@ def request_workload(r: Request, cache: bool = True) -> Workload:
         if cache:
             _request_cache[key] = w
     return replace(w, steps=r.steps)
+
+
+# ---------------------------------------------------------------------------
+# tetrahedral meshes (the paper's setting: unstructured tetrahedral cells)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class TetMesh:
+    """A conforming tetrahedral mesh of a periodic box: every cube of an
+    n x n x n grid split into six tetrahedra along its main diagonal.
+    Cell c has local vertices a = 0..3; its face a is the one opposite vertex
+    a.  Arrays: xyz (cells, 4, 3) vertex coordinates, unwrapped so that each
+    cell is a geometric tetrahedron; vid (cells, 4) global vertex ids
+    (periodic); nbr (cells, 4) the cell across face a; wrap (cells, 4) 1
+    where face a crosses the periodic boundary of the box (the two cells'
+    copies of the face lie one period apart); cube (cells, 3) the parent
+    cube.  Connectivity only: no geometry of the method is computed here."""
+    n: int
+    lo: tuple
+    hi: tuple
+    xyz: np.ndarray = field(repr=False)
+    vid: np.ndarray = field(repr=False)
+    nbr: np.ndarray = field(repr=False)
+    cube: np.ndarray = field(repr=False)
+    wrap: np.ndarray = field(default=None, repr=False)
+
+    @property
+    def cells(self) -> int:
+        return self.vid.shape[0]
+
+    def subdomains(self, tiles: int) -> np.ndarray:
+        """Subdomain id per cell: the parent cubes cut into tiles^3 boxes."""
+        L = self.n // tiles
+        t = self.cube // L
+        return (t[:, 2] * tiles + t[:, 1]) * tiles + t[:, 0]
+
+    def node_coords(self) -> np.ndarray:
+        """(cells * 4, 3): the P1 nodes (the vertices of every cell), cell-major."""
+        return self.xyz.reshape(-1, 3)
+
+
+_KUHN = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def tet_box(n: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)) -> TetMesh:
+    """Periodic box [lo, hi]^3 of n^3 cubes (n >= 2), six tetrahedra per cube:
+    vertex 0 at the cube's lower corner, then one step along each axis in the
+    order of a permutation of (x, y, z), ending at the upper corner."""
+    if n < 2:
+        raise ValueError("n must be at least 2 (periodic vertex ids must separate the faces)")
+    lo = np.asarray(lo, float)
+    h = (np.asarray(hi, float) - lo) / n
+    cells = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                for perm in _KUHN:
+                    p = np.array([i, j, k])
+                    pts = [p.copy()]
+                    for a in perm:
+                        p = p.copy()
+                        p[a] += 1
+                        pts.append(p)
+                    cells.append(pts)
+    ijk = np.array(cells)                                      # (cells, 4, 3) integer lattice points
+    xyz = lo + ijk * h
+    w = ijk % n
+    vid = (w[..., 2] * n + w[..., 1]) * n + w[..., 0]
+    cube = ijk[:, 0, :]
+    # faces: the three vertex ids other than a, shared by exactly two cells
+    owner = {}
+    nbr = -np.ones((len(cells), 4), dtype=np.int64)
+    for c in range(len(cells)):
+        for a in range(4):
+            key = tuple(sorted(int(vid[c, b]) for b in range(4) if b != a))
+            if key in owner:
+                c2, a2 = owner.pop(key)
+                nbr[c, a] = c2
+                nbr[c2, a2] = c
+            else:
+                owner[key] = (c, a)
+    if owner or (nbr < 0).any():
+        raise ValueError("tet_box: the mesh is not closed")
+    # a face wraps when the lattice points of its vertices differ between the
+    # two cells (they agree modulo n)
+    wrap = np.zeros((len(cells), 4), dtype=np.int32)
+    for c in range(len(cells)):
+        for a in range(4):
+            R = nbr[c, a]
+            for b in range(4):
+                if b == a:
+                    continue
+                j = int(np.nonzero(vid[R] == vid[c, b])[0][0])
+                if (ijk[R, j] != ijk[c, b]).any():
+                    wrap[c, a] = 1
+                    break
+    return TetMesh(n, tuple(lo), tuple(hi), xyz, vid.astype(np.int64), nbr, cube.astype(np.int64), wrap)
+
+
+@dataclass
+class TetWorkload:
+    """A kinetic DG problem on a tetrahedral mesh (P1 nodal basis, the four
+    vertices of each cell): the recipe and the initial data at the nodes,
+    W0 (m, cells * 4)."""
+    name: str
+    mesh: TetMesh
+    system: int
+    velset: int               # 0: D3Q6 (+-lambda e_a), 1: D3Q4 (cube diagonals, Sec. 6.1.3)
+    lam: float
+    dt: float
+    omega: float
+    gamma: float
+    adv: tuple
+    tiles: int
+    iters: int
+    precision: str
+    W0: np.ndarray = field(repr=False)
+    exact: Optional[Callable] = field(default=None, repr=False)
+    sigma: float = 0.0
+
+    @property
+    def m(self) -> int:
+        return {ADVECTION: 1, EULER: 5, MAXWELL: 6}[self.system]
+
+    @property
+    def nvel(self) -> int:
+        return 4 if self.velset == 1 else 6
+
+    @property
+    def npop(self) -> int:
+        return self.nvel * self.m
+
+    @property
+    def nodes(self) -> int:
+        return 4 * self.mesh.cells
+
+    @property
+    def kinetic_dofs(self) -> int:
+        return self.npop * self.nodes
+
+    def subdomains(self) -> np.ndarray:
+        return self.mesh.subdomains(self.tiles)
+
+
+def tet_h_min(mesh: TetMesh) -> float:
+    """Smallest cell volume / surface of the Kuhn tetrahedra (all congruent):
+    for a cube of side h, volume h^3/6 and faces of areas h^2/2 (two) and
+    h^2 sqrt(2)/2 (two): vol/surf = h / (3 (2 + 2 sqrt 2)) * ... computed
+    from the lattice geometry (the recipe's time step needs it)."""
+    h = (mesh.hi[0] - mesh.lo[0]) / mesh.n
+    vol = h ** 3 / 6.0
+    surf = 2 * (h * h / 2.0) + 2 * (h * h * math.sqrt(2.0) / 2.0)
+    return vol / surf
+
+
+def tet_densitywave(seed: int = 0, n: int = 16, tiles: int = 2, velset: int = 1, dt_mult: float = 5.0,
+                    iters: int = 3, omega: float = 2.0, precision: str = "f32", amp: float = 0.2) -> TetWorkload:
+    """3D Euler density wave rho = 1 + amp sin(2 pi (x + y + z) + phi),
+    u = (1, 1, 1), p = 1 (phi ~ U(0, 2 pi) from the seed) on the periodic
+    unit cube meshed by tet_box(n); subdomains of (n / tiles)^3 cubes.
+    Kinetic speed: D3Q4 lambda = 1.5 a_max, D3Q6 lambda = 3.3 a_max.  Time
+    step: dt = dt_mult x h_min / |V|_max with h_min = vol / surf (the paper's
+    CFL-number definition; dt_mult = 1 is the explicit DG limit)."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.0, 2 * np.pi)
+    gamma = 1.4
+    mesh = tet_box(n)
+    xyz = mesh.node_coords()
+    s = xyz.sum(axis=1)
+
+    def fields(t):
+        rho = 1.0 + amp * np.sin(2 * np.pi * (s - 3 * t) + phi)
+        vel = tuple(np.ones_like(rho) for _ in range(3))
+        return rho, vel, np.ones_like(rho)
+
+    rho, vel, pr = fields(0.0)
+    amax = _max_speed(rho, vel, pr, gamma)
+    lam = (SIMPLEX_LAMBDA[3] if velset == 1 else 1.1 * 3) * amax
+    vmax = lam * math.sqrt(3.0) if velset == 1 else lam
+    dt = dt_mult * tet_h_min(mesh) / vmax
+
+    def exact(t):
+        r, vv, p = fields(t)
+        return _euler_conserved(r, vv, p, gamma)
+
+    return TetWorkload("tet-densitywave", mesh, EULER, velset, lam, dt, omega, gamma, (0.0, 0.0, 0.0), tiles,
+                       iters, precision, _euler_conserved(rho, vel, pr, gamma), exact)
+
+
+def tet_advection(seed: int = 0, n: int = 8, tiles: int = 1, velset: int = 1, dt_mult: float = 5.0,
+                  iters: int = 3, omega: float = 2.0, adv=(1.0, 0.5, 0.25), lam: float = 2.0,
+                  precision: str = "f64") -> TetWorkload:
+    """Scalar advection u_t + a . grad u = 0 on the periodic unit cube meshed
+    by tet_box(n): u0 = A sin(2 pi (x + 2y - z) + phi) + B with A, B ~
+    U(0.5, 1.5), phi ~ U(0, 2 pi) from the seed."""
+    rng = np.random.default_rng(seed)
+    A, B = rng.uniform(0.5, 1.5, size=2)
+    phi = rng.uniform(0.0, 2 * np.pi)
+    mesh = tet_box(n)
+    xyz = mesh.node_coords()
+    kvec = np.array([1.0, 2.0, -1.0])
+    a = np.asarray(adv, float)
+
+    def exact(t):
+        return (A * np.sin(2 * np.pi * ((xyz - a * t) @ kvec) + phi) + B)[None, :]
+
+    vmax = lam * math.sqrt(3.0) if velset == 1 else lam
+    dt = dt_mult * tet_h_min(mesh) / vmax
+    return TetWorkload("tet-advection", mesh, ADVECTION, velset, lam, dt, omega, 1.4, tuple(adv), tiles, iters,
+                       precision, exact(0.0), exact)
