@@ -497,6 +497,105 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# tetrahedral meshes (the paper's setting)
+# ---------------------------------------------------------------------------
+
+TET_DESC = "tet-densitywave-euler-32^3x6-tets-P1-D3Q4-4^3sub-K3"
+
+
+def run_tet(args):
+    """3D Euler density wave on the periodic unit cube meshed by 32^3 cubes x
+    6 tetrahedra (196,608 cells, P1 nodes at the vertices), D3Q4 (the
+    paper's cube diagonals), 4^3 subdomains of 8^3 cubes, K = 3,
+    dt = 5 h_min / |V|, FP32: 15,728,640 kinetic DOF (63 MB).  A step is K
+    sweep launches (one block per subdomain and velocity, walking the
+    breadth-first levels) and one extrapolation + relaxation launch."""
+    import torch
+    import workloads
+    import paper_2212_11010_gb300 as kin
+    ws, rank, dev = _setup_gpu()
+    w = workloads.tet_densitywave(seed=0, n=32, tiles=4, velset=1, dt_mult=5.0)
+    prec = args.precision or w.precision
+    kprec = kin.KIN_FP32 if prec == "f32" else kin.KIN_FP64
+    stream = torch.cuda.Stream()
+    ctx = kin.TetContext.from_workload(w, precision=kprec, torch_alloc=True, stream=stream.cuda_stream)
+    ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+    dofs = w.kinetic_dofs
+    esize = 4 if prec == "f32" else 8
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+    for _ in range(args.warmup):
+        flush_l2()
+        ctx.step(1)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for a, b in ev:
+            flush_l2()
+            a.record(stream)
+            ctx.step(1)
+            b.record(stream)
+        stream.synchronize()
+        clk.mark(t0, time.perf_counter())
+    ms_per_step, value = replica_aggregate(float(np.sum([a.elapsed_time(b) for a, b in ev])), args.steps, dofs)
+    peak, peak_kind = measured_peak_hbm()
+    # bytes a step must move with K literal sweeps: every sweep reads f^n and
+    # writes its iterate, the final launch reads f^n and the last iterate and
+    # writes f^{n+1} -- (2 K + 3) x the state; the floor of one read and one
+    # write (8 B per DOF in FP32) is what the roofline fraction is taken on
+    algo_bytes = ALGO_BYTES_PER_DOF[prec] * dofs
+    achieved = algo_bytes / (ms_per_step * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": TET_DESC, "cells": w.mesh.cells, "kinetic_dofs": dofs, "state_bytes": esize * dofs,
+                   "subdomains": int(w.subdomains().max()) + 1, "l2": "256 MB written before every timed step",
+                   "launches_per_step": w.iters + 1},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
+                     "note": f"K + 1 = {w.iters + 1} launches per step move about {2 * w.iters + 3} x the state"},
+        "gpu_launches": (w.iters + 1) * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        # accuracy on the same recipe at 8^3 cubes (the oracle at 32^3 would
+        # take minutes), after the same number of steps
+        import oracle
+        ws8 = workloads.tet_densitywave(seed=0, n=8, tiles=1, velset=1, dt_mult=5.0)
+        nst = args.warmup + args.steps
+        with kin.TetContext.from_workload(ws8, precision=kprec) as c8:
+            c8.set_state(np.ascontiguousarray(ws8.W0.reshape(-1)))
+            c8.step(nst)
+            W8, f8 = c8.get_state(), c8.get_kinetic()
+        oracle.set_threads(os.cpu_count() or 1)
+        P = oracle.tet_problem(ws8)
+        T = oracle.TetMesh.from_workload(ws8)
+        fo = oracle.tet_init(P, T, ws8.W0)
+        oracle.tet_step(P, T, fo, nst)
+        Wo = oracle.tet_moments(P, T, fo).reshape(ws8.m, -1)
+        W8 = W8.reshape(ws8.m, -1)
+        line["error_vs_oracle"] = {
+            "W_linf": max(float(np.abs(W8[v] - Wo[v]).max() / np.abs(Wo[v]).max()) for v in range(ws8.m)),
+            "f_max": float(np.abs(f8 - fo).max() / np.abs(fo).max()), "steps": nst,
+            "sample": "the same recipe on 8^3 cubes x 6 tetrahedra, one subdomain"}
+        # the oracle's rate on that sample, all cores and one
+        t0 = time.perf_counter()
+        oracle.tet_step(P, T, fo, 2)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 2 * ws8.kinetic_dofs / el, "unit": UNIT, "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": f"2 steps of the 8^3-cube recipe in {el:.1f} s",
+                                "host": host_cpu()}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # batched (default)
 # ---------------------------------------------------------------------------
 
@@ -873,7 +972,7 @@ def main():
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "serving", "vortex2d", "densitywave3d", "advection1d",
                              "vortex2d-d2q3", "densitywave3d-d3q4", "maxwell3d", "vortex2d-512-p3",
-                             "maxwell3d-dirichlet"])
+                             "maxwell3d-dirichlet", "tet-densitywave"])
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--schedule", default="auto", choices=["auto", "per-type", "mixed"],
                     help="batch schedule: chosen by the autotuner (auto) or fixed")
@@ -889,6 +988,8 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "tet-densitywave":
+        run_tet(args)
     else:
         run_ours(args)
 

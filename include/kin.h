@@ -166,6 +166,48 @@ typedef struct {
 kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, double dt,
                       const kin_opts* opts, kin_ctx** out);
 
+/* Tetrahedral meshes -- the paper's own setting (Sec. 3.1: unstructured
+ * tetrahedral cells with n_f = 4 faces; Sec. 3.2: the cell graph oriented by
+ * V, a DAG swept in breadth-first topological order; Sec. 5.1: subdomains
+ * coupled by eq. ibvp).  Basis: P1 nodal, the four vertices of each cell,
+ * with exact integrals.  Face a of a cell is the face opposite its local
+ * vertex a; a face with |V.N| <= 1e-12 |V| is parallel to V (no flux).
+ * Meshes are periodic: every face has a neighbour.  A face is a subdomain
+ * interface -- its inflow comes from the previous iterate -- when the cell
+ * across it lies in another subdomain or when wrap marks it (a face across
+ * the periodic boundary, so that a subdomain wrapping around the box is
+ * acyclic).  All arrays are host memory, read during kin_create_tet only. */
+typedef struct {
+    int ncells;
+    const double* xyz;       /* [cell][4][3] vertex coordinates (one geometric tetrahedron per cell) */
+    const long long* vid;    /* [cell][4] global vertex ids: nodes that meet across a face share an id */
+    const long long* nbr;    /* [cell][4] the cell across face a                                      */
+    const int* sub;          /* [cell] subdomain id, 0..nsub-1                                        */
+    const int* wrap;         /* [cell][4] 1: face a crosses the periodic boundary (may be NULL: none) */
+} kin_tetmesh;
+
+/* Create a context on a tetrahedral mesh.  model: system (advection, Euler
+ * with m = 5, Maxwell with m = 6), velset KIN_D3Q6 or KIN_D3Q4 (the cube
+ * diagonals of Sec. 6.1.3), lambda, gamma, adv, omega, sigma as for
+ * kin_create.  opts: iters, precision, stream, the allocator hooks and
+ * mem_budget are used; tiles, block, threads and stages are not (the
+ * subdomains come from mesh->sub).  The FP64 set-up inverts the local
+ * implicit block of every (cell, velocity) on the GPU; the host orients the
+ * faces and sorts every subdomain breadth-first into levels.  Storage of W
+ * and f: [v][cell][a] and [pop][cell][a] (a the local vertex, pop = k m + v;
+ * D3Q6 k = 2 axis + sign, D3Q4 k in the order (+,+,+), (+,-,-), (-,+,-),
+ * (-,-,+)).  The context then takes kin_set_state, kin_set_kinetic,
+ * kin_step, kin_get_state, kin_get_kinetic, kin_diag (mass only),
+ * kin_query, kin_sync and kin_destroy; kin_set_boundary and batches return
+ * KIN_EINVAL.  Each step is K sweep launches (one thread block per
+ * (subdomain, velocity) walking the levels) and one launch for the
+ * Crank-Nicolson extrapolation and the relaxation.  Errors: KIN_EINVAL (bad
+ * arguments or topology: a neighbour out of range, a face whose vertices are
+ * not in the neighbour, a degenerate cell, a cycle in a subdomain's oriented
+ * graph), KIN_EBUDGET, KIN_ENOMEM, KIN_ECUDA. */
+kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, double dt, const kin_opts* opts,
+                          kin_ctx** out);
+
 /* Set f = M(W) at every node (Sec. 2.2: the natural initial choice
  * F_k = M_k(W(., 0))).  W: m * nodes doubles in the storage order above, on
  * the host (on_device = 0, pageable or pinned; copied before return) or on

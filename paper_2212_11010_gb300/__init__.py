@@ -33,7 +33,7 @@ STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
 EXPORTED = ["kin_create", "kin_set_state", "kin_set_kinetic", "kin_step", "kin_get_state",
             "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error",
             "kin_step_noalloc", "kin_batch_create", "kin_batch_create_ex", "kin_batch_step", "kin_batch_sync",
-            "kin_batch_destroy", "kin_batch_last_error", "kin_set_boundary", "kin_batch_info"]
+            "kin_batch_destroy", "kin_batch_last_error", "kin_set_boundary", "kin_batch_info", "kin_create_tet"]
 
 
 class KinError(RuntimeError):
@@ -65,6 +65,12 @@ class kin_opts(ctypes.Structure):
                 ("debug_flags", ctypes.c_int), ("threads", ctypes.c_int), ("stages", ctypes.c_int)]
 
 
+class kin_tetmesh(ctypes.Structure):
+    _fields_ = [("ncells", ctypes.c_int), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("vid", ctypes.POINTER(ctypes.c_longlong)), ("nbr", ctypes.POINTER(ctypes.c_longlong)),
+                ("sub", ctypes.POINTER(ctypes.c_int)), ("wrap", ctypes.POINTER(ctypes.c_int))]
+
+
 class kin_info(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("degree", ctypes.c_int), ("m", ctypes.c_int),
                 ("nvel", ctypes.c_int), ("npop", ctypes.c_int), ("nodes_per_cell", ctypes.c_int),
@@ -93,6 +99,8 @@ def load_library():
     dp = ctypes.POINTER(ctypes.c_double)
     lib.kin_create.argtypes = [ctypes.POINTER(kin_mesh), ctypes.POINTER(kin_model), ctypes.c_int,
                                ctypes.c_double, ctypes.POINTER(kin_opts), ctypes.POINTER(vp)]
+    lib.kin_create_tet.argtypes = [ctypes.POINTER(kin_tetmesh), ctypes.POINTER(kin_model), ctypes.c_double,
+                                   ctypes.POINTER(kin_opts), ctypes.POINTER(vp)]
     lib.kin_set_state.argtypes = [vp, vp, sz, ctypes.c_int]
     lib.kin_set_kinetic.argtypes = [vp, vp, sz, ctypes.c_int]
     lib.kin_set_boundary.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, sz]
@@ -171,6 +179,14 @@ def kin_create(mesh: kin_mesh, model: kin_model, degree: int, dt: float, opts: k
     ctx = ctypes.c_void_p()
     st = lib.kin_create(ctypes.byref(mesh), ctypes.byref(model), degree, dt, ctypes.byref(opts),
                         ctypes.byref(ctx))
+    _check(None, st)
+    return ctx
+
+
+def kin_create_tet(mesh: kin_tetmesh, model: kin_model, dt: float, opts: kin_opts):
+    lib = load_library()
+    ctx = ctypes.c_void_p()
+    st = lib.kin_create_tet(ctypes.byref(mesh), ctypes.byref(model), dt, ctypes.byref(opts), ctypes.byref(ctx))
     _check(None, st)
     return ctx
 
@@ -448,3 +464,35 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+class TetContext(Context):
+    """Owning wrapper of a kin_ctx on a tetrahedral mesh (kin_create_tet);
+    the state and step methods are Context's."""
+
+    def __init__(self, xyz, vid, nbr, sub, wrap, system, velset, lam, dt, omega=2.0, gamma=1.4,
+                 adv=(0.0, 0.0, 0.0), sigma=0.0, iters=3, precision=KIN_FP64, mem_budget=0, stream=None,
+                 torch_alloc=False):
+        self._arrays = [np.ascontiguousarray(xyz, dtype=np.float64), np.ascontiguousarray(vid, dtype=np.int64),
+                        np.ascontiguousarray(nbr, dtype=np.int64), np.ascontiguousarray(sub, dtype=np.int32),
+                        np.ascontiguousarray(wrap, dtype=np.int32)]
+        x, v, nb, sb, wr = self._arrays
+        self.mesh = kin_tetmesh(v.shape[0], x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                v.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                nb.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                sb.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                wr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        _, self.model, self.opts = make_args(3, (1, 1, 1), (0, 0, 0), (1, 1, 1), system, lam, omega=omega,
+                                             gamma=gamma, adv=adv, iters=iters, precision=precision,
+                                             mem_budget=mem_budget, stream=stream, torch_alloc=torch_alloc,
+                                             velset=velset, sigma=sigma)
+        self.ctx = kin_create_tet(self.mesh, self.model, dt, self.opts)
+        self.info = kin_query(self.ctx)
+
+    @classmethod
+    def from_workload(cls, w, precision=None, **kw):
+        prec = precision if precision is not None else (KIN_FP32 if w.precision == "f32" else KIN_FP64)
+        m = w.mesh
+        return cls(m.xyz, m.vid, m.nbr, w.subdomains(), m.wrap, w.system, KIN_D3Q4 if w.velset == 1 else KIN_D3Q6,
+                   w.lam, w.dt, omega=w.omega, gamma=w.gamma, adv=w.adv, sigma=w.sigma, iters=w.iters,
+                   precision=prec, **kw)

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkin.so")
 SOURCES = ["kin_api.cu", "kin_aux.cu", "kin_step_d1.cu", "kin_step_d2.cu", "kin_step_d3.cu",
-           "kin_simplex.cu"]
+           "kin_simplex.cu", "kin_tet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", os.path.join(ROOT, "include")]

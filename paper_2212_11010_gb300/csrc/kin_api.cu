@@ -68,6 +68,18 @@ struct kin_ctx {
     void* sxtr[2][3] = {};
     size_t sx_smem = 0;
     int sx_stride = 0;
+    // tetrahedral meshes
+    bool tet = false;
+    int nsub = 0;
+    int tsgn[4][3] = {};
+    void* tcoef = nullptr;            // T records [velocity][cell][kTetRec]
+    int* torder = nullptr;            // [velocity][cells]
+    int* tlstart = nullptr;           // [velocity][nsub + 1]
+    int* tbounds = nullptr;           // level boundaries
+    int* tfnodes = nullptr;           // [cell][4][3]
+    int* tiface = nullptr;            // [cell]
+    void* titer[2] = {nullptr, nullptr};   // subdomain iterates
+    std::vector<double> tvol;         // host: cell volumes, for the mass diagnostic
     bool have_state = false;
     long long steps_done = 0;
     bool poisoned = false;
@@ -466,6 +478,51 @@ static kin_status sx_step(kin_ctx* c)
     return KIN_OK;
 }
 
+// ---- tetrahedral meshes: launch arguments and one step ----
+static TetArgs tet_args(const kin_ctx* c)
+{
+    TetArgs a;
+    memset(&a, 0, sizeof a);
+    a.ncells = (int)c->cells;
+    a.nvel = c->nvel;
+    a.m = c->m;
+    a.npop = c->npop;
+    a.nsub = c->nsub;
+    a.system = c->system;
+    a.velset = c->simplex ? 1 : 0;
+    a.nodes = (long long)c->nodes;
+    a.coef = c->tcoef;
+    a.order = c->torder;
+    a.lstart = c->tlstart;
+    a.bounds = c->tbounds;
+    a.fnodes = c->tfnodes;
+    a.iface = c->tiface;
+    a.f = c->f;
+    a.lambda = c->lambda;
+    a.gamma = c->gamma;
+    a.omega = c->omega;
+    a.mu = c->system == KIN_MAXWELL ? (1.0 - 0.5 * c->sigma * c->dt) / (1.0 + 0.5 * c->sigma * c->dt) : 1.0;
+    for (int i = 0; i < 3; ++i) a.adv[i] = c->adv[i];
+    for (int k = 0; k < 4; ++k)
+        for (int i = 0; i < 3; ++i) a.sgn[k][i] = c->tsgn[k][i];
+    return a;
+}
+
+// One step S(dt) on a tetrahedral mesh: K sweeps (iterate p in titer[p & 1],
+// iterate 0 = f^n), then the Crank-Nicolson extrapolation with the
+// relaxation.
+static kin_status tet_step(kin_ctx* c)
+{
+    const TetArgs a = tet_args(c);
+    const int prec = c->precision == KIN_FP32;
+    for (int p = 1; p <= c->iters; ++p) {
+        const void* prev = p == 1 ? c->f : c->titer[(p - 1) & 1];
+        KIN_CUDA(c, tet_launch_sweep(a, prev, c->titer[p & 1], prec, c->stream));
+    }
+    KIN_CUDA(c, tet_launch_relax(a, c->titer[c->iters & 1], prec, c->stream));
+    return KIN_OK;
+}
+
 extern "C" {
 
 kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, double dt,
@@ -776,6 +833,270 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
     return KIN_OK;
 }
 
+kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, double dt, const kin_opts* opts,
+                          kin_ctx** out)
+{
+    if (!out) return fail(nullptr, KIN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mesh || !model || !opts) return fail(nullptr, KIN_EINVAL, "mesh, model and opts must be non-NULL");
+    if (mesh->ncells < 1 || !mesh->xyz || !mesh->vid || !mesh->nbr || !mesh->sub)
+        return fail(nullptr, KIN_EINVAL, "the mesh needs cells, xyz, vid, nbr and sub");
+    if (model->system != KIN_ADVECTION && model->system != KIN_EULER && model->system != KIN_MAXWELL)
+        return fail(nullptr, KIN_EINVAL, "unknown system %d", model->system);
+    if (model->velset != KIN_D3Q6 && model->velset != KIN_D3Q4)
+        return fail(nullptr, KIN_EINVAL, "tetrahedral meshes take the D3Q6 or D3Q4 velocity set");
+    if (model->system == KIN_MAXWELL && !(model->sigma >= 0.0))
+        return fail(nullptr, KIN_EINVAL, "the conductivity sigma must be >= 0");
+    if (!(model->lambda > 0) || !(dt > 0)) return fail(nullptr, KIN_EINVAL, "lambda and dt must be positive");
+    if (!(model->omega >= 1.0 && model->omega <= 2.0)) return fail(nullptr, KIN_EINVAL, "omega must lie in [1, 2]");
+    if (model->system == KIN_EULER && !(model->gamma > 1.0)) return fail(nullptr, KIN_EINVAL, "gamma must exceed 1");
+    if (opts->iters < 1) return fail(nullptr, KIN_EINVAL, "iters must be >= 1");
+    if (opts->precision != KIN_FP64 && opts->precision != KIN_FP32)
+        return fail(nullptr, KIN_EINVAL, "unknown precision %d", opts->precision);
+    if ((opts->alloc == nullptr) != (opts->free == nullptr))
+        return fail(nullptr, KIN_EINVAL, "alloc and free hooks must be given together");
+    const int n = mesh->ncells;
+    // topology: neighbours in range, every face's vertices present in the
+    // neighbour (the nodes that meet across the face), subdomains 0..nsub-1
+    int nsub = 0;
+    std::vector<int> fnodes((size_t)n * 12), iface(n, 0);
+    for (int cc = 0; cc < n; ++cc) {
+        if (mesh->sub[cc] < 0) return fail(nullptr, KIN_EINVAL, "cell %d: negative subdomain", cc);
+        nsub = std::max(nsub, mesh->sub[cc] + 1);
+        for (int a = 0; a < 4; ++a) {
+            const long long R = mesh->nbr[(size_t)cc * 4 + a];
+            if (R < 0 || R >= n || R == cc)
+                return fail(nullptr, KIN_EINVAL, "cell %d face %d: neighbour %lld out of range", cc, a, R);
+            int jj = 0;
+            for (int j = 0; j < 4; ++j) {
+                if (j == a) continue;
+                int found = -1;
+                for (int q = 0; q < 4; ++q)
+                    if (mesh->vid[R * 4 + q] == mesh->vid[(size_t)cc * 4 + j]) found = q;
+                if (found < 0)
+                    return fail(nullptr, KIN_EINVAL, "cell %d face %d: vertex %d not in the neighbour", cc, a, j);
+                fnodes[(size_t)cc * 12 + a * 3 + jj++] = (int)(R * 4 + found);
+            }
+            const bool wrap = mesh->wrap && mesh->wrap[(size_t)cc * 4 + a];
+            if (wrap || mesh->sub[R] != mesh->sub[cc]) iface[cc] |= 1 << a;
+        }
+    }
+    if ((long long)n * 4 * 36 > (1LL << 31))
+        return fail(nullptr, KIN_EINVAL, "too many cells for 32-bit node indices");
+
+    kin_ctx* c = new (std::nothrow) kin_ctx();
+    if (!c) return fail(nullptr, KIN_ENOMEM, "host allocation failed");
+    c->tet = true;
+    c->dim = 3;
+    c->degree = 1;
+    c->system = model->system;
+    c->m = model->system == KIN_MAXWELL ? 6 : (model->system == KIN_EULER ? 5 : 1);
+    c->simplex = model->velset == KIN_D3Q4;
+    c->nvel = c->simplex ? 4 : 6;
+    c->npop = c->nvel * c->m;
+    c->NP = 2;
+    c->NN = 4;
+    c->sigma = model->sigma;
+    c->lambda = model->lambda;
+    c->gamma = model->gamma;
+    c->omega = model->omega;
+    c->dt = dt;
+    c->iters = opts->iters;
+    c->precision = opts->precision;
+    c->esize = opts->precision == KIN_FP32 ? 4 : 8;
+    c->stream = (cudaStream_t)opts->stream;
+    c->alloc = opts->alloc;
+    c->dealloc = opts->free;
+    c->alloc_user = opts->alloc_user;
+    c->budget = opts->mem_budget;
+    for (int a = 0; a < 3; ++a) c->adv[a] = model->adv[a];
+    c->cells = (size_t)n;
+    c->nodes = (size_t)n * 4;
+    c->nsub = nsub;
+    static const int s3[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+    double vel[6][3] = {};
+    for (int k = 0; k < c->nvel; ++k)
+        for (int a = 0; a < 3; ++a) {
+            if (c->simplex) {
+                c->tsgn[k][a] = s3[k][a];
+                vel[k][a] = c->lambda * s3[k][a];
+            } else {
+                vel[k][a] = a == k / 2 ? (k % 2 ? -c->lambda : c->lambda) : 0.0;
+            }
+        }
+
+    // faces oriented by every velocity (the same FP64 formulas as the setup
+    // kernel: N_a = -grad psi_a / |grad psi_a|; |V.N| <= 1e-12 |V| is parallel)
+    std::vector<unsigned char> ftype((size_t)c->nvel * n, 0);
+    c->tvol.assign(n, 0.0);
+    for (int cc = 0; cc < n; ++cc) {
+        const double* x = mesh->xyz + (size_t)cc * 12;
+        double e[3][3];
+        for (int b = 0; b < 3; ++b)
+            for (int i = 0; i < 3; ++i) e[b][i] = x[3 * (b + 1) + i] - x[i];
+        auto cross = [](const double* a, const double* b, double* r) {
+            r[0] = a[1] * b[2] - a[2] * b[1];
+            r[1] = a[2] * b[0] - a[0] * b[2];
+            r[2] = a[0] * b[1] - a[1] * b[0];
+        };
+        double g[4][3], c12[3], c20[3], c01[3];
+        cross(e[1], e[2], c12);
+        cross(e[2], e[0], c20);
+        cross(e[0], e[1], c01);
+        const double det = e[0][0] * c12[0] + e[0][1] * c12[1] + e[0][2] * c12[2];
+        if (!(std::fabs(det) > 0)) {
+            delete c;
+            return fail(nullptr, KIN_EINVAL, "cell %d is degenerate", cc);
+        }
+        c->tvol[cc] = std::fabs(det) / 6.0;
+        for (int i = 0; i < 3; ++i) {
+            g[1][i] = c12[i] / det;
+            g[2][i] = c20[i] / det;
+            g[3][i] = c01[i] / det;
+            g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+        }
+        for (int k = 0; k < c->nvel; ++k) {
+            const double vmag = std::sqrt(vel[k][0] * vel[k][0] + vel[k][1] * vel[k][1] + vel[k][2] * vel[k][2]);
+            unsigned char t = 0;
+            for (int a = 0; a < 4; ++a) {
+                const double gl = std::sqrt(g[a][0] * g[a][0] + g[a][1] * g[a][1] + g[a][2] * g[a][2]);
+                const double vn = -(vel[k][0] * g[a][0] + vel[k][1] * g[a][1] + vel[k][2] * g[a][2]) / gl;
+                if (std::fabs(vn) > 1e-12 * vmag) t |= (unsigned char)((vn < 0 ? 1 : 2) << (2 * a));
+            }
+            ftype[(size_t)k * n + cc] = t;
+        }
+    }
+    // breadth-first levels of every subdomain's oriented graph, per velocity
+    std::vector<int> order((size_t)c->nvel * n), lstart((size_t)c->nvel * (nsub + 1)), bounds;
+    {
+        std::vector<int> bysub(n), sstart(nsub + 1, 0);
+        for (int cc = 0; cc < n; ++cc) sstart[mesh->sub[cc] + 1]++;
+        for (int q = 0; q < nsub; ++q) sstart[q + 1] += sstart[q];
+        std::vector<int> fill(sstart.begin(), sstart.end() - 1);
+        for (int cc = 0; cc < n; ++cc) bysub[fill[mesh->sub[cc]]++] = cc;
+        std::vector<int> indeg(n), lev(n);
+        for (int k = 0; k < c->nvel; ++k) {
+            int* ord = order.data() + (size_t)k * n;
+            for (int cc = 0; cc < n; ++cc) {
+                indeg[cc] = 0;
+                lev[cc] = 0;
+                for (int a = 0; a < 4; ++a)
+                    if (((ftype[(size_t)k * n + cc] >> (2 * a)) & 3) == 1 && !((iface[cc] >> a) & 1)) indeg[cc]++;
+            }
+            int pos = 0;
+            for (int q = 0; q < nsub; ++q) {
+                lstart[(size_t)k * (nsub + 1) + q] = (int)bounds.size();
+                const int head0 = pos;
+                for (int i = sstart[q]; i < sstart[q + 1]; ++i)
+                    if (indeg[bysub[i]] == 0) ord[pos++] = bysub[i];
+                int head = head0;
+                while (head < pos) {
+                    const int cc = ord[head++];
+                    for (int a = 0; a < 4; ++a) {
+                        if (((ftype[(size_t)k * n + cc] >> (2 * a)) & 3) != 2 || ((iface[cc] >> a) & 1)) continue;
+                        const int R = (int)mesh->nbr[(size_t)cc * 4 + a];
+                        lev[R] = std::max(lev[R], lev[cc] + 1);
+                        if (--indeg[R] == 0) ord[pos++] = R;
+                    }
+                }
+                if (pos - head0 != sstart[q + 1] - sstart[q]) {
+                    delete c;
+                    return fail(nullptr, KIN_EINVAL, "subdomain %d: the oriented cell graph of velocity %d has a cycle "
+                                "(a subdomain wrapping the periodic box needs its wrap faces marked)", q, k);
+                }
+                // the breadth-first order lists the cells level by level
+                std::stable_sort(ord + head0, ord + pos, [&](int x, int y) { return lev[x] < lev[y]; });
+                for (int i = head0; i < pos; ++i)
+                    if (i == head0 || lev[ord[i]] != lev[ord[i - 1]]) bounds.push_back(i);
+            }
+            lstart[(size_t)k * (nsub + 1) + nsub] = (int)bounds.size();
+            bounds.push_back(pos);
+        }
+    }
+
+    kin_status st;
+    void* p;
+#define ALLOC(dst, bytes)                                                 \
+    do {                                                                  \
+        st = dev_alloc(c, (bytes), &p);                                   \
+        if (st != KIN_OK) {                                               \
+            g_create_error = c->err;                                      \
+            release_all(c);                                               \
+            delete c;                                                     \
+            return st;                                                    \
+        }                                                                 \
+        dst = (decltype(dst))p;                                           \
+    } while (0)
+    ALLOC(c->f, c->nodes * c->npop * c->esize);
+    for (int i = 0; i < 2; ++i) ALLOC(c->titer[i], c->nodes * c->npop * c->esize);
+    ALLOC(c->tcoef, (size_t)c->nvel * n * kTetRec * c->esize);
+    ALLOC(c->torder, sizeof(int) * order.size());
+    ALLOC(c->tlstart, sizeof(int) * lstart.size());
+    ALLOC(c->tbounds, sizeof(int) * bounds.size());
+    ALLOC(c->tfnodes, sizeof(int) * fnodes.size());
+    ALLOC(c->tiface, sizeof(int) * iface.size());
+    ALLOC(c->Wbuf, sizeof(double) * c->m * c->nodes);
+    ALLOC(c->errword, sizeof(int) * 4);
+    // FP64 setup scratch: vertex coordinates, face types, FP64 records
+    double* xyz_d = nullptr;
+    unsigned char* ft_d = nullptr;
+    double* c64_d = nullptr;
+    ALLOC(xyz_d, sizeof(double) * 12 * (size_t)n);
+    ALLOC(ft_d, ftype.size());
+    ALLOC(c64_d, sizeof(double) * (size_t)c->nvel * n * kTetRec);
+#undef ALLOC
+    cudaError_t e = cudaMemcpyAsync(c->torder, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tlstart, lstart.data(), sizeof(int) * lstart.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tbounds, bounds.data(), sizeof(int) * bounds.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tfnodes, fnodes.data(), sizeof(int) * fnodes.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->tiface, iface.data(), sizeof(int) * iface.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(xyz_d, mesh->xyz, sizeof(double) * 12 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ft_d, ftype.data(), ftype.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->errword, 0, sizeof(int) * 4, c->stream);
+    if (e == cudaSuccess) {
+        TetSetupArgs sa;
+        memset(&sa, 0, sizeof sa);
+        sa.ncells = n;
+        sa.nvel = c->nvel;
+        sa.xyz = xyz_d;
+        for (int k = 0; k < 6; ++k)
+            for (int i = 0; i < 3; ++i) sa.vel[k][i] = vel[k][i];
+        sa.dt = dt;
+        sa.ftype = ft_d;
+        sa.c64 = c64_d;
+        sa.c32 = c->esize == 4 ? (float*)c->tcoef : nullptr;
+        e = tet_launch_setup(sa, c->stream);
+    }
+    if (e == cudaSuccess && c->esize == 8)
+        e = cudaMemcpyAsync(c->tcoef, c64_d, sizeof(double) * (size_t)c->nvel * n * kTetRec,
+                            cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(nullptr, KIN_ECUDA, "tetrahedral set-up failed: %s", cudaGetErrorString(e));
+        release_all(c);
+        delete c;
+        return KIN_ECUDA;
+    }
+    // the set-up scratch goes back (the last three allocations)
+    for (int i = 0; i < 3; ++i) {
+        auto b = c->blocks.back();
+        if (c->dealloc) c->dealloc(b.first, b.second, (void*)c->stream, c->alloc_user);
+        else cudaFree(b.first);
+        c->bytes_held -= b.second;
+        c->blocks.pop_back();
+    }
+    c->grid = (int)(c->nsub * c->nvel);
+    c->threads = 128;
+    *out = c;
+    return KIN_OK;
+}
+
 kin_status kin_set_state(kin_ctx* c, const double* W, size_t n_values, int on_device)
 {
     kin_status st = check_usable(c);
@@ -789,7 +1110,9 @@ kin_status kin_set_state(kin_ctx* c, const double* W, size_t n_values, int on_de
                                     c->stream));
         src = c->Wbuf;
     }
-    if (c->simplex) {
+    if (c->tet) {
+        KIN_CUDA(c, tet_launch_init(tet_args(c), src, c->precision == KIN_FP32, c->stream));
+    } else if (c->simplex) {
         KIN_CUDA(c, sx_launch_init(sx_args(c), src, c->precision == KIN_FP32, c->stream));
     } else {
         KIN_CUDA(c, launch_init(point_args(c), src, c->f, c->precision == KIN_FP32, c->stream));
@@ -814,7 +1137,7 @@ kin_status kin_set_kinetic(kin_ctx* c, const void* f, size_t n_values, int on_de
         return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
     KIN_CUDA(c, cudaMemcpyAsync(c->f, f, n_values * c->esize,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    if (!c->simplex) {
+    if (!c->simplex && !c->tet) {
         st = launch_step(c, 1);
         if (st) return st;
     }
@@ -840,6 +1163,7 @@ kin_status kin_set_boundary(kin_ctx* c, int axis, int side, const double* W, siz
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    if (c->tet) return fail(c, KIN_EINVAL, "tetrahedral meshes are periodic: no boundary faces");
     if (axis < 0 || axis >= c->dim || !c->inflow[axis])
         return fail(c, KIN_EINVAL, "axis %d is not an inflow axis", axis);
     if (side != 0 && side != 1) return fail(c, KIN_EINVAL, "side must be 0 (lower) or 1 (upper)");
@@ -875,7 +1199,7 @@ kin_status kin_step(kin_ctx* c, int nsteps)
     if (const char* face = missing_boundary(c))
         return fail(c, KIN_ESTATE, "the %s face of an inflow axis has no boundary state (kin_set_boundary)", face);
     for (int s = 0; s < nsteps; ++s) {
-        st = c->simplex ? sx_step(c) : launch_step(c, 0);
+        st = c->tet ? tet_step(c) : (c->simplex ? sx_step(c) : launch_step(c, 0));
         if (st) return st;
         c->steps_done++;
     }
@@ -925,6 +1249,28 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
     if (!c->have_state) return fail(c, KIN_ESTATE, "no state has been set");
     if ((next_defect || iter_residual) && (c->inflow[0] || c->inflow[1] || c->inflow[2]))
         return fail(c, KIN_EINVAL, "next_defect and iter_residual are not available with inflow axes");
+    if (c->tet) {
+        // the exact integral of the P1 moments: sum over cells of |L|/4 times
+        // the sum of W over the cell's nodes (FP64 moments, host reduction)
+        if (next_defect || iter_residual)
+            return fail(c, KIN_EINVAL, "next_defect and iter_residual are not available on tetrahedral meshes");
+        if (mass_per_var) {
+            KIN_CUDA(c, launch_moments(point_args(c), c->f, c->Wbuf, c->precision == KIN_FP32, c->stream));
+            std::vector<double> W((size_t)c->m * c->nodes);
+            KIN_CUDA(c, cudaMemcpyAsync(W.data(), c->Wbuf, sizeof(double) * W.size(), cudaMemcpyDeviceToHost,
+                                        c->stream));
+            KIN_CUDA(c, cudaStreamSynchronize(c->stream));
+            for (int v = 0; v < c->m; ++v) {
+                double acc = 0.0;
+                for (size_t cc = 0; cc < c->cells; ++cc) {
+                    const double* w = W.data() + (size_t)v * c->nodes + cc * 4;
+                    acc += c->tvol[cc] / 4.0 * (w[0] + w[1] + w[2] + w[3]);
+                }
+                mass_per_var[v] = acc;
+            }
+        }
+        return KIN_OK;
+    }
     double host[8] = {0};
     if (mass_per_var) {
         KIN_CUDA(c, launch_mass(point_args(c), c->f, c->gll, c->partial, c->result,
@@ -1161,6 +1507,8 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
             return batch_fail(nullptr, KIN_ESTATE, "member %d has an inflow face without a boundary state", i);
         if (members[i]->simplex)
             return batch_fail(nullptr, KIN_EINVAL, "member %d uses a d+1 velocity set (not batched)", i);
+        if (members[i]->tet)
+            return batch_fail(nullptr, KIN_EINVAL, "member %d has a tetrahedral mesh (not batched)", i);
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return batch_fail(nullptr, KIN_EINVAL, "member %d repeats member %d", i, j);
     }

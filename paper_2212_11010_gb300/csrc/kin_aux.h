@@ -83,6 +83,39 @@ cudaError_t sx_launch_sweep(const SxArgs& a, int prec, size_t smem, cudaStream_t
 cudaError_t sx_launch_relax(const SxArgs& a, int prec, cudaStream_t st);
 cudaError_t sx_launch_init(const SxArgs& a, const double* W, int prec, cudaStream_t st);
 
+// ---- tetrahedral meshes (kin_tet.cu) ----
+constexpr int kTetRec = 24;       // coefficient slots per (velocity, cell)
+
+struct TetSetupArgs {
+    int ncells, nvel;
+    const double* xyz;            // [cell][4][3] vertex coordinates
+    double vel[6][3];             // V_k
+    double dt;
+    const unsigned char* ftype;   // [velocity][cell]: 2 bits per face a: 1 inflow, 2 outflow, 0 parallel
+    double* c64;                  // [velocity][cell][kTetRec] FP64 records
+    float* c32;                   // FP32 copy (NULL for FP64)
+};
+
+struct TetArgs {
+    int ncells, nvel, m, npop, nsub, system, velset;
+    long long nodes;              // 4 ncells
+    const void* coef;             // T records [velocity][cell][kTetRec]
+    const int* order;             // [velocity][ncells]: cells by subdomain, then breadth-first
+    const int* lstart;            // [velocity][nsub + 1]: first level index of each subdomain in bounds
+    const int* bounds;            // level l of the order holds positions [bounds[l], bounds[l + 1])
+    const int* fnodes;            // [cell][face a][3]: the neighbour's node (R * 4 + j) at each vertex of the face
+    const int* iface;             // [cell]: bit a set when face a is a subdomain interface
+    void* f;                      // T [pop][cell][4]
+    double lambda, gamma, omega, mu;
+    double adv[3];
+    int sgn[4][3];                // D3Q4 velocity signs
+};
+
+cudaError_t tet_launch_setup(const TetSetupArgs& a, cudaStream_t st);
+cudaError_t tet_launch_sweep(const TetArgs& a, const void* prev, void* cur, int prec, cudaStream_t st);
+cudaError_t tet_launch_relax(const TetArgs& a, const void* star, int prec, cudaStream_t st);
+cudaError_t tet_launch_init(const TetArgs& a, const double* W, int prec, cudaStream_t st);
+
 cudaError_t launch_setup(const SetupArgs& a, cudaStream_t st);
 cudaError_t launch_init(const PointArgs& a, const double* W, void* f, int prec, cudaStream_t st);
 // host: the 2d-velocity Maxwellians M[(2a + s) m + v] of one state (FP64)

@@ -1,0 +1,343 @@
+// kin_tet.cu -- the kinetic DG step on tetrahedral meshes (the paper's
+// setting: Sec. 3.1 with tetrahedral cells, Sec. 3.2 downwind order, Sec. 5.1
+// subdomain iteration).
+//
+// Basis: P1 Lagrange functions of each cell's four vertices, every integral
+// exact: mass |L|/20 (1 + delta_ij); volume term (V . grad psi_i) |L|/4; face
+// mass |F|/12 (1 + delta_ij) on the face's three vertices.  The implicit half
+// step of Crank-Nicolson (tau = dt/2) of one cell reads
+//   A f* = M f^n + tau sum_{inflow faces} |V.N| F f_R,
+//   A = M + tau (-K + sum_{outflow faces} (V.N) F),
+// and f^{n+1} = 2 f* - f^n.  Since A 1 = M 1 + tau sum_in |V.N| F 1 (the weak
+// form of a constant), the kernels solve it in difference form about the
+// cell's first node value r: f* - r 1 = A^{-1} [M (f^n - r 1) + tau sum_in
+// |V.N| F (f_R - r 1)], exact for constant states whatever the rounding of
+// A^{-1} (as on the Cartesian path).
+//
+// Downwind order (Sec. 3.2): for each velocity the host orients the faces,
+// and inside every subdomain sorts the cells breadth-first into levels
+// (cells of one level have no upwind neighbour in the same level).  A step
+// is K launches of the sweep kernel -- one block per (subdomain, velocity),
+// walking the levels with a barrier between them, every thread one cell of
+// the level for all m variables -- and one pointwise launch for the
+// Crank-Nicolson extrapolation and the relaxation.  Iteration p reads the
+// neighbour's iterate p-1 across a subdomain interface (a face to another
+// subdomain, or across the periodic boundary) and the current iterate
+// inside (eq. ibvp); iterate 0 is f^n.
+#include "kin_aux.h"
+#include "kin_device.cuh"
+
+#include <algorithm>
+
+namespace kin {
+
+// ---------------------------------------------------------------------------
+// FP64 setup: per (velocity, cell) the record
+//   [0, 16)  A^{-1} (row-major)      [16]  |L| / 20
+//   [17, 21) tau |V.N_a| |F_a| / 12 on inflow faces a, else 0
+// ---------------------------------------------------------------------------
+
+__global__ void tet_setup_kernel(TetSetupArgs A)
+{
+    const long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= (long long)A.ncells * A.nvel) return;
+    const int k = (int)(id / A.ncells);
+    const int c = (int)(id - (long long)k * A.ncells);
+    const double* x = A.xyz + (size_t)c * 12;
+    const double V[3] = {A.vel[k][0], A.vel[k][1], A.vel[k][2]};
+    double e[3][3];
+    for (int b = 0; b < 3; ++b)
+        for (int i = 0; i < 3; ++i) e[b][i] = x[3 * (b + 1) + i] - x[i];
+    auto cross = [](const double* a, const double* b, double* r) {
+        r[0] = a[1] * b[2] - a[2] * b[1];
+        r[1] = a[2] * b[0] - a[0] * b[2];
+        r[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    double c12[3], c20[3], c01[3];
+    cross(e[1], e[2], c12);
+    cross(e[2], e[0], c20);
+    cross(e[0], e[1], c01);
+    const double det = e[0][0] * c12[0] + e[0][1] * c12[1] + e[0][2] * c12[2];
+    const double vol = fabs(det) / 6.0;
+    double grad[4][3];
+    for (int i = 0; i < 3; ++i) {
+        grad[1][i] = c12[i] / det;
+        grad[2][i] = c20[i] / det;
+        grad[3][i] = c01[i] / det;
+        grad[0][i] = -(grad[1][i] + grad[2][i] + grad[3][i]);
+    }
+    double area[4];
+    for (int a = 0; a < 4; ++a) {
+        // |F_a| = 3 |L| |grad psi_a|: the face opposite vertex a
+        const double g2 = grad[a][0] * grad[a][0] + grad[a][1] * grad[a][1] + grad[a][2] * grad[a][2];
+        area[a] = 3.0 * vol * sqrt(g2);
+    }
+    const double tau = 0.5 * A.dt;
+    double M[4][8];
+    for (int i = 0; i < 4; ++i) {
+        const double vg = V[0] * grad[i][0] + V[1] * grad[i][1] + V[2] * grad[i][2];
+        for (int j = 0; j < 4; ++j) {
+            M[i][j] = vol / 20.0 * (i == j ? 2.0 : 1.0) - tau * vg * vol / 4.0;
+            M[i][4 + j] = i == j ? 1.0 : 0.0;
+        }
+    }
+    const unsigned char ft = A.ftype[(size_t)k * A.ncells + c];
+    double cin[4] = {0, 0, 0, 0};
+    for (int a = 0; a < 4; ++a) {
+        const int t = (ft >> (2 * a)) & 3;          // 1 inflow, 2 outflow, 0 parallel
+        if (t == 0) continue;
+        // V.N_a with N_a = -grad psi_a / |grad psi_a|
+        const double gl = sqrt(grad[a][0] * grad[a][0] + grad[a][1] * grad[a][1] + grad[a][2] * grad[a][2]);
+        const double vn = -(V[0] * grad[a][0] + V[1] * grad[a][1] + V[2] * grad[a][2]) / gl;
+        if (t == 2) {
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j)
+                    if (i != a && j != a) M[i][j] += tau * vn * area[a] / 12.0 * (i == j ? 2.0 : 1.0);
+        } else {
+            cin[a] = tau * fabs(vn) * area[a] / 12.0;
+        }
+    }
+    // Gauss-Jordan inverse with partial pivoting
+    for (int col = 0; col < 4; ++col) {
+        int p = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (fabs(M[r][col]) > fabs(M[p][col])) p = r;
+        if (p != col)
+            for (int j = 0; j < 8; ++j) {
+                const double t = M[col][j];
+                M[col][j] = M[p][j];
+                M[p][j] = t;
+            }
+        const double d = 1.0 / M[col][col];
+        for (int j = 0; j < 8; ++j) M[col][j] *= d;
+        for (int r = 0; r < 4; ++r) {
+            if (r == col) continue;
+            const double l = M[r][col];
+            for (int j = 0; j < 8; ++j) M[r][j] -= l * M[col][j];
+        }
+    }
+    double* rec = A.c64 + ((size_t)k * A.ncells + c) * kTetRec;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) rec[i * 4 + j] = M[i][4 + j];
+    rec[16] = vol / 20.0;
+    for (int a = 0; a < 4; ++a) rec[17 + a] = cin[a];
+    for (int q = 21; q < kTetRec; ++q) rec[q] = 0.0;
+    if (A.c32) {
+        float* r32 = A.c32 + ((size_t)k * A.ncells + c) * kTetRec;
+        for (int q = 0; q < kTetRec; ++q) r32[q] = (float)rec[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// sweep: one block per (subdomain, velocity), levels in order
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(128) tet_sweep_kernel(TetArgs A, const T* __restrict__ prev, T* cur)
+{
+    const int s = blockIdx.x, k = blockIdx.y;
+    const int* __restrict__ order = A.order + (size_t)k * A.ncells;
+    const int lb = A.lstart[k * (A.nsub + 1) + s], le = A.lstart[k * (A.nsub + 1) + s + 1];
+    const T* __restrict__ coef = static_cast<const T*>(A.coef) + (size_t)k * A.ncells * kTetRec;
+    const T* __restrict__ fn = static_cast<const T*>(A.f);
+    const long long nodes = A.nodes;
+    for (int l = lb; l < le; ++l) {
+        const int p0 = A.bounds[l], p1 = A.bounds[l + 1];
+        for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
+            const int c = order[q];
+            const T* rec = coef + (size_t)c * kTetRec;
+            T Ai[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) Ai[i] = rec[i];
+            const T m20 = rec[16];
+            T cin[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) cin[a] = rec[17 + a];
+            const int* fnode = A.fnodes + (size_t)c * 12;
+            const int iface = A.iface[c];
+            for (int v = 0; v < A.m; ++v) {
+                const long long pop = (long long)(k * A.m + v) * nodes;
+                T u[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) u[i] = fn[pop + (size_t)c * 4 + i];
+                const T r = u[0];
+                T du[4], sum = T(0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    du[i] = u[i] - r;
+                    sum += du[i];
+                }
+                T rhs[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) rhs[i] = m20 * (sum + du[i]);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    if (cin[a] == T(0)) continue;
+                    const T* src = ((iface >> a) & 1) ? prev : cur;
+                    // the neighbour's values at this cell's face vertices (j != a, ascending)
+                    T g[4] = {T(0), T(0), T(0), T(0)};
+                    T gs = T(0);
+                    int jj = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (j == a) continue;
+                        g[j] = src[pop + fnode[a * 3 + jj]] - r;
+                        gs += g[j];
+                        ++jj;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (i != a) rhs[i] = fma(cin[a], gs + g[i], rhs[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    T x = Ai[i * 4] * rhs[0];
+#pragma unroll
+                    for (int j = 1; j < 4; ++j) x = fma(Ai[i * 4 + j], rhs[j], x);
+                    cur[pop + (size_t)c * 4 + i] = x + r;
+                }
+            }
+        }
+        __syncthreads();     // the next level reads this level's cells
+    }
+}
+
+// ---------------------------------------------------------------------------
+// equilibria and relaxation at the nodes
+// ---------------------------------------------------------------------------
+
+// Q^a(W) of the system (Euler, scalar advection or Maxwell).
+template <typename V>
+__device__ __forceinline__ void tet_flux(const TetArgs& A, const V* W, int a, V* Q)
+{
+    if (A.system == kAdvection) {
+        Q[0] = V(A.adv[a]) * W[0];
+        return;
+    }
+    if (A.system == kMaxwell) {
+        maxwell_flux(W, a, Q, V(0));
+        return;
+    }
+    V ke = V(0);
+    for (int b = 0; b < 3; ++b) ke = fma(W[1 + b], W[1 + b], ke);
+    const V inv = V(1) / W[0];
+    const V pr = V(A.gamma - 1.0) * (W[4] - V(0.5) * ke * inv);
+    const V ua = W[1 + a] * inv;
+    Q[0] = W[1 + a];
+    for (int b = 0; b < 3; ++b) Q[1 + b] = W[1 + b] * ua + (b == a ? pr : V(0));
+    Q[4] = (W[4] + pr) * ua;
+}
+
+// Equilibria of all populations: D3Q6 M_{a+-} = W/6 +- Q^a/(2 lambda);
+// D3Q4 (cube diagonals V_k = lambda s_k, Sec. 6.1.3)
+// M_k = W/4 + sum_a s_k^a Q^a / (4 lambda), which solves eq. maxwell_def.
+template <typename V>
+__device__ __forceinline__ void tet_equilibria(const TetArgs& A, const V* W, V* M)
+{
+    V Q[3][kMaxVars];
+    for (int a = 0; a < 3; ++a) tet_flux(A, W, a, Q[a]);
+    const int m = A.m;
+    if (A.velset == 1) {
+        const V il = V(1.0 / (4.0 * A.lambda));
+        for (int k = 0; k < 4; ++k)
+            for (int v = 0; v < m; ++v) {
+                V q = V(0);
+                for (int a = 0; a < 3; ++a) q += V(A.sgn[k][a]) * Q[a][v];
+                M[k * m + v] = fma(q, il, W[v] * V(0.25));
+            }
+    } else {
+        const V il = V(1.0 / (2.0 * A.lambda));
+        for (int a = 0; a < 3; ++a)
+            for (int v = 0; v < m; ++v) {
+                const V base = div2d<3>(W[v]);
+                M[(2 * a) * m + v] = base + Q[a][v] * il;
+                M[(2 * a + 1) * m + v] = base - Q[a][v] * il;
+            }
+    }
+}
+
+// f^{n+1} = 2 f* - f^n, then W = sum_k f_k (Kahan in FP32) and the
+// relaxation f <- omega M(W) + (1 - omega) f (eq. over_relaxation); Maxwell
+// with conductivity relaxes about the equilibrium after the source step,
+// f <- M(W+) + (1 - omega)(f - M(W-)).
+template <typename T>
+__global__ void tet_relax_kernel(TetArgs A, const T* __restrict__ star)
+{
+    T* f = static_cast<T*>(A.f);
+    const long long nodes = A.nodes;
+    const int npop = A.npop, m = A.m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        T fk[kMaxPop];
+        for (int p = 0; p < npop; ++p) fk[p] = fma(T(2), star[p * nodes + i], -f[p * nodes + i]);
+        T W[kMaxVars];
+        for (int v = 0; v < m; ++v) {
+            Acc<T> acc;
+            for (int k = 0; k < A.nvel; ++k) acc.add(fk[k * m + v]);
+            W[v] = acc.s;
+        }
+        T Mm[kMaxPop];
+        tet_equilibria(A, W, Mm);
+        const T om = T(A.omega);
+        if (A.system == kMaxwell) {
+            T Wp[kMaxVars], Mp[kMaxPop];
+            for (int v = 0; v < m; ++v) Wp[v] = v < 3 ? T(A.mu) * W[v] : W[v];
+            tet_equilibria(A, Wp, Mp);
+            for (int p = 0; p < npop; ++p) f[p * nodes + i] = fma(T(1) - om, fk[p] - Mm[p], Mp[p]);
+        } else if (A.omega == 2.0) {
+            for (int p = 0; p < npop; ++p) f[p * nodes + i] = fma(T(2), Mm[p], -fk[p]);
+        } else {
+            for (int p = 0; p < npop; ++p) f[p * nodes + i] = om * Mm[p] + (T(1) - om) * fk[p];
+        }
+    }
+}
+
+// f = M(W) from the FP64 macroscopic state (Sec. 2.2 initialisation).
+template <typename T>
+__global__ void tet_init_kernel(TetArgs A, const double* __restrict__ W0)
+{
+    T* f = static_cast<T*>(A.f);
+    const long long nodes = A.nodes;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        double W[kMaxVars], M[kMaxPop];
+        for (int v = 0; v < A.m; ++v) W[v] = W0[v * nodes + i];
+        tet_equilibria(A, W, M);
+        for (int p = 0; p < A.npop; ++p) f[p * nodes + i] = (T)M[p];
+    }
+}
+
+cudaError_t tet_launch_setup(const TetSetupArgs& a, cudaStream_t st)
+{
+    const long long n = (long long)a.ncells * a.nvel;
+    tet_setup_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t tet_launch_sweep(const TetArgs& a, const void* prev, void* cur, int prec, cudaStream_t st)
+{
+    const dim3 grid(a.nsub, a.nvel);
+    if (prec == 1)
+        tet_sweep_kernel<float><<<grid, 128, 0, st>>>(a, static_cast<const float*>(prev), static_cast<float*>(cur));
+    else
+        tet_sweep_kernel<double><<<grid, 128, 0, st>>>(a, static_cast<const double*>(prev), static_cast<double*>(cur));
+    return cudaGetLastError();
+}
+
+cudaError_t tet_launch_relax(const TetArgs& a, const void* star, int prec, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)std::min<long long>((a.nodes + 255) / 256, 152LL * 8);
+    if (prec == 1) tet_relax_kernel<float><<<grid, 256, 0, st>>>(a, static_cast<const float*>(star));
+    else tet_relax_kernel<double><<<grid, 256, 0, st>>>(a, static_cast<const double*>(star));
+    return cudaGetLastError();
+}
+
+cudaError_t tet_launch_init(const TetArgs& a, const double* W, int prec, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)std::min<long long>((a.nodes + 255) / 256, 152LL * 8);
+    if (prec == 1) tet_init_kernel<float><<<grid, 256, 0, st>>>(a, W);
+    else tet_init_kernel<double><<<grid, 256, 0, st>>>(a, W);
+    return cudaGetLastError();
+}
+
+}  // namespace kin

@@ -511,10 +511,10 @@ class TetWorkload:
 
 
 def tet_h_min(mesh: TetMesh) -> float:
-    """Smallest cell volume / surface of the Kuhn tetrahedra (all congruent):
-    for a cube of side h, volume h^3/6 and faces of areas h^2/2 (two) and
-    h^2 sqrt(2)/2 (two): vol/surf = h / (3 (2 + 2 sqrt 2)) * ... computed
-    from the lattice geometry (the recipe's time step needs it)."""
+    """h_min = volume / surface of the Kuhn tetrahedra (all congruent), the
+    length in the paper's CFL-number definition that the recipes' time steps
+    use: for a cube of side h a cell has volume h^3/6 and two faces of area
+    h^2/2 and two of area h^2 sqrt(2)/2."""
     h = (mesh.hi[0] - mesh.lo[0]) / mesh.n
     vol = h ** 3 / 6.0
     surf = 2 * (h * h / 2.0) + 2 * (h * h * math.sqrt(2.0) / 2.0)
@@ -576,3 +576,29 @@ def tet_advection(seed: int = 0, n: int = 8, tiles: int = 1, velset: int = 1, dt
     dt = dt_mult * tet_h_min(mesh) / vmax
     return TetWorkload("tet-advection", mesh, ADVECTION, velset, lam, dt, omega, 1.4, tuple(adv), tiles, iters,
                        precision, exact(0.0), exact)
+
+
+def tet_maxwell(seed: int = 0, n: int = 8, tiles: int = 2, velset: int = 0, dt_mult: float = 5.0,
+                iters: int = 3, omega: float = 2.0, sigma: float = 0.0, precision: str = "f64") -> TetWorkload:
+    """Maxwell's equations (light speed 1) on the periodic unit cube meshed by
+    tet_box(n): the three plane waves of maxwell3d sampled at the P1 nodes.
+    Kinetic speed: D3Q6 lambda = 3.3, D3Q4 lambda = 1.5 (|V_k| = 1.5 sqrt 3)."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.0, 2 * np.pi, size=3)
+    amp = rng.uniform(0.5, 1.5, size=3)
+    mesh = tet_box(n)
+    xyz = mesh.node_coords()
+
+    def fields(t):
+        W = np.zeros((6, xyz.shape[0]))
+        for k, (a, e, h) in enumerate(((0, 1, 2), (1, 2, 0), (2, 0, 1))):
+            c = amp[k] * np.cos(2 * np.pi * (xyz[:, a] - t) + phi[k])
+            W[e] += c
+            W[3 + h] += c
+        return W
+
+    lam = 1.5 if velset == 1 else 3.3
+    vmax = lam * math.sqrt(3.0) if velset == 1 else lam
+    dt = dt_mult * tet_h_min(mesh) / vmax
+    return TetWorkload("tet-maxwell", mesh, MAXWELL, velset, lam, dt, omega, 1.4, (0.0, 0.0, 0.0), tiles, iters,
+                       precision, fields(0.0), fields if sigma == 0.0 else None, sigma)
