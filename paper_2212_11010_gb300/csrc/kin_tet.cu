@@ -28,6 +28,7 @@
 #include "kin_device.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace kin {
 
@@ -132,6 +133,41 @@ __global__ void tet_setup_kernel(TetSetupArgs A)
 // sweep: one block per (subdomain, velocity), levels in order
 // ---------------------------------------------------------------------------
 
+// The four node values of a cell as one vector access (FP32: 16 bytes; the
+// cell's nodes are contiguous and every population slab starts 16-byte
+// aligned).
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, T (&u)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        u[0] = q.x;
+        u[1] = q.y;
+        u[2] = q.z;
+        u[3] = q.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        u[0] = a.x;
+        u[1] = a.y;
+        u[2] = b.x;
+        u[3] = b.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store4(T* p, const T (&u)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(u[0], u[1], u[2], u[3]);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(u[0], u[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(u[2], u[3]);
+    }
+}
+
+// Every thread takes one (cell, variable) pair of the level: the m threads
+// of a cell read the same coefficient record (one broadcast), and a level of
+// c cells offers c m independent solves.
 template <typename T>
 __global__ void __launch_bounds__(128) tet_sweep_kernel(TetArgs A, const T* __restrict__ prev, T* cur)
 {
@@ -141,62 +177,59 @@ __global__ void __launch_bounds__(128) tet_sweep_kernel(TetArgs A, const T* __re
     const T* __restrict__ coef = static_cast<const T*>(A.coef) + (size_t)k * A.ncells * kTetRec;
     const T* __restrict__ fn = static_cast<const T*>(A.f);
     const long long nodes = A.nodes;
+    const int m = A.m;
     for (int l = lb; l < le; ++l) {
         const int p0 = A.bounds[l], p1 = A.bounds[l + 1];
-        for (int q = p0 + threadIdx.x; q < p1; q += blockDim.x) {
-            const int c = order[q];
+        const int items = (p1 - p0) * m;
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int q = it / m, v = it - q * m;
+            const int c = order[p0 + q];
             const T* rec = coef + (size_t)c * kTetRec;
-            T Ai[16];
+            const long long pop = (long long)(k * m + v) * nodes;
+            T u[4];
+            load4(fn + pop + (size_t)c * 4, u);
+            const T r = u[0];
+            T du[4], sum = T(0);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) Ai[i] = rec[i];
+            for (int i = 0; i < 4; ++i) {
+                du[i] = u[i] - r;
+                sum += du[i];
+            }
             const T m20 = rec[16];
-            T cin[4];
+            T rhs[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) cin[a] = rec[17 + a];
+            for (int i = 0; i < 4; ++i) rhs[i] = m20 * (sum + du[i]);
             const int* fnode = A.fnodes + (size_t)c * 12;
             const int iface = A.iface[c];
-            for (int v = 0; v < A.m; ++v) {
-                const long long pop = (long long)(k * A.m + v) * nodes;
-                T u[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) u[i] = fn[pop + (size_t)c * 4 + i];
-                const T r = u[0];
-                T du[4], sum = T(0);
+            for (int a = 0; a < 4; ++a) {
+                const T ca = rec[17 + a];
+                if (ca == T(0)) continue;
+                const T* src = ((iface >> a) & 1) ? prev : cur;
+                // the neighbour's values at this cell's face vertices (j != a, ascending)
+                T g[4] = {T(0), T(0), T(0), T(0)};
+                T gs = T(0);
+                int jj = 0;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    du[i] = u[i] - r;
-                    sum += du[i];
-                }
-                T rhs[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) rhs[i] = m20 * (sum + du[i]);
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    if (cin[a] == T(0)) continue;
-                    const T* src = ((iface >> a) & 1) ? prev : cur;
-                    // the neighbour's values at this cell's face vertices (j != a, ascending)
-                    T g[4] = {T(0), T(0), T(0), T(0)};
-                    T gs = T(0);
-                    int jj = 0;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (j == a) continue;
-                        g[j] = src[pop + fnode[a * 3 + jj]] - r;
-                        gs += g[j];
-                        ++jj;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (i != a) rhs[i] = fma(cin[a], gs + g[i], rhs[i]);
+                for (int j = 0; j < 4; ++j) {
+                    if (j == a) continue;
+                    g[j] = src[pop + fnode[a * 3 + jj]] - r;
+                    gs += g[j];
+                    ++jj;
                 }
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    T x = Ai[i * 4] * rhs[0];
-#pragma unroll
-                    for (int j = 1; j < 4; ++j) x = fma(Ai[i * 4 + j], rhs[j], x);
-                    cur[pop + (size_t)c * 4 + i] = x + r;
-                }
+                for (int i = 0; i < 4; ++i)
+                    if (i != a) rhs[i] = fma(ca, gs + g[i], rhs[i]);
             }
+            T x[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                T acc = rec[i * 4] * rhs[0];
+#pragma unroll
+                for (int j = 1; j < 4; ++j) acc = fma(rec[i * 4 + j], rhs[j], acc);
+                x[i] = acc + r;
+            }
+            store4(cur + pop + (size_t)c * 4, x);
         }
         __syncthreads();     // the next level reads this level's cells
     }
@@ -207,47 +240,54 @@ __global__ void __launch_bounds__(128) tet_sweep_kernel(TetArgs A, const T* __re
 // ---------------------------------------------------------------------------
 
 // Q^a(W) of the system (Euler, scalar advection or Maxwell).
-template <typename V>
+template <int SYS, typename V>
 __device__ __forceinline__ void tet_flux(const TetArgs& A, const V* W, int a, V* Q)
 {
-    if (A.system == kAdvection) {
+    if constexpr (SYS == kAdvection) {
         Q[0] = V(A.adv[a]) * W[0];
-        return;
-    }
-    if (A.system == kMaxwell) {
+    } else if constexpr (SYS == kMaxwell) {
         maxwell_flux(W, a, Q, V(0));
-        return;
+    } else {
+        V ke = V(0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) ke = fma(W[1 + b], W[1 + b], ke);
+        const V inv = V(1) / W[0];
+        const V pr = V(A.gamma - 1.0) * (W[4] - V(0.5) * ke * inv);
+        const V ua = W[1 + a] * inv;
+        Q[0] = W[1 + a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Q[1 + b] = W[1 + b] * ua + (b == a ? pr : V(0));
+        Q[4] = (W[4] + pr) * ua;
     }
-    V ke = V(0);
-    for (int b = 0; b < 3; ++b) ke = fma(W[1 + b], W[1 + b], ke);
-    const V inv = V(1) / W[0];
-    const V pr = V(A.gamma - 1.0) * (W[4] - V(0.5) * ke * inv);
-    const V ua = W[1 + a] * inv;
-    Q[0] = W[1 + a];
-    for (int b = 0; b < 3; ++b) Q[1 + b] = W[1 + b] * ua + (b == a ? pr : V(0));
-    Q[4] = (W[4] + pr) * ua;
 }
 
 // Equilibria of all populations: D3Q6 M_{a+-} = W/6 +- Q^a/(2 lambda);
 // D3Q4 (cube diagonals V_k = lambda s_k, Sec. 6.1.3)
 // M_k = W/4 + sum_a s_k^a Q^a / (4 lambda), which solves eq. maxwell_def.
-template <typename V>
+template <int SYS, int VS, typename V>
 __device__ __forceinline__ void tet_equilibria(const TetArgs& A, const V* W, V* M)
 {
-    V Q[3][kMaxVars];
-    for (int a = 0; a < 3; ++a) tet_flux(A, W, a, Q[a]);
-    const int m = A.m;
-    if (A.velset == 1) {
+    constexpr int m = nvars(3, SYS);
+    V Q[3][m];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tet_flux<SYS>(A, W, a, Q[a]);
+    if constexpr (VS == 1) {
+        constexpr int sg[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
         const V il = V(1.0 / (4.0 * A.lambda));
+#pragma unroll
         for (int k = 0; k < 4; ++k)
+#pragma unroll
             for (int v = 0; v < m; ++v) {
-                V q = V(0);
-                for (int a = 0; a < 3; ++a) q += V(A.sgn[k][a]) * Q[a][v];
+                V q = V(sg[k][0]) * Q[0][v];
+                q = fma(V(sg[k][1]), Q[1][v], q);
+                q = fma(V(sg[k][2]), Q[2][v], q);
                 M[k * m + v] = fma(q, il, W[v] * V(0.25));
             }
     } else {
         const V il = V(1.0 / (2.0 * A.lambda));
+#pragma unroll
         for (int a = 0; a < 3; ++a)
+#pragma unroll
             for (int v = 0; v < m; ++v) {
                 const V base = div2d<3>(W[v]);
                 M[(2 * a) * m + v] = base + Q[a][v] * il;
@@ -259,53 +299,103 @@ __device__ __forceinline__ void tet_equilibria(const TetArgs& A, const V* W, V* 
 // f^{n+1} = 2 f* - f^n, then W = sum_k f_k (Kahan in FP32) and the
 // relaxation f <- omega M(W) + (1 - omega) f (eq. over_relaxation); Maxwell
 // with conductivity relaxes about the equilibrium after the source step,
-// f <- M(W+) + (1 - omega)(f - M(W-)).
-template <typename T>
-__global__ void tet_relax_kernel(TetArgs A, const T* __restrict__ star)
+// f <- M(W+) + (1 - omega)(f - M(W-)).  Compiled per system and velocity
+// set, so that every population stays in registers.
+template <int SYS, int VS, typename T>
+__global__ void __launch_bounds__(256) tet_relax_kernel(TetArgs A, const T* __restrict__ star)
 {
+    constexpr int m = nvars(3, SYS), NV = VS == 1 ? 4 : 6, NPOP = NV * m;
     T* f = static_cast<T*>(A.f);
     const long long nodes = A.nodes;
-    const int npop = A.npop, m = A.m;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
-        T fk[kMaxPop];
-        for (int p = 0; p < npop; ++p) fk[p] = fma(T(2), star[p * nodes + i], -f[p * nodes + i]);
-        T W[kMaxVars];
+        T fk[NPOP];
+#pragma unroll
+        for (int p = 0; p < NPOP; ++p) fk[p] = fma(T(2), star[p * nodes + i], -f[p * nodes + i]);
+        T W[m];
+#pragma unroll
         for (int v = 0; v < m; ++v) {
             Acc<T> acc;
-            for (int k = 0; k < A.nvel; ++k) acc.add(fk[k * m + v]);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) acc.add(fk[k * m + v]);
             W[v] = acc.s;
         }
-        T Mm[kMaxPop];
-        tet_equilibria(A, W, Mm);
+        T Mm[NPOP];
+        tet_equilibria<SYS, VS>(A, W, Mm);
         const T om = T(A.omega);
-        if (A.system == kMaxwell) {
-            T Wp[kMaxVars], Mp[kMaxPop];
+        if constexpr (SYS == kMaxwell) {
+            T Wp[m], Mp[NPOP];
+#pragma unroll
             for (int v = 0; v < m; ++v) Wp[v] = v < 3 ? T(A.mu) * W[v] : W[v];
-            tet_equilibria(A, Wp, Mp);
-            for (int p = 0; p < npop; ++p) f[p * nodes + i] = fma(T(1) - om, fk[p] - Mm[p], Mp[p]);
-        } else if (A.omega == 2.0) {
-            for (int p = 0; p < npop; ++p) f[p * nodes + i] = fma(T(2), Mm[p], -fk[p]);
+            tet_equilibria<SYS, VS>(A, Wp, Mp);
+#pragma unroll
+            for (int p = 0; p < NPOP; ++p) f[p * nodes + i] = fma(T(1) - om, fk[p] - Mm[p], Mp[p]);
         } else {
-            for (int p = 0; p < npop; ++p) f[p * nodes + i] = om * Mm[p] + (T(1) - om) * fk[p];
+            if (A.omega == 2.0) {
+#pragma unroll
+                for (int p = 0; p < NPOP; ++p) f[p * nodes + i] = fma(T(2), Mm[p], -fk[p]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < NPOP; ++p) f[p * nodes + i] = om * Mm[p] + (T(1) - om) * fk[p];
+            }
         }
     }
 }
 
 // f = M(W) from the FP64 macroscopic state (Sec. 2.2 initialisation).
-template <typename T>
+template <int SYS, int VS, typename T>
 __global__ void tet_init_kernel(TetArgs A, const double* __restrict__ W0)
 {
+    constexpr int m = nvars(3, SYS), NPOP = (VS == 1 ? 4 : 6) * m;
     T* f = static_cast<T*>(A.f);
     const long long nodes = A.nodes;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
-        double W[kMaxVars], M[kMaxPop];
-        for (int v = 0; v < A.m; ++v) W[v] = W0[v * nodes + i];
-        tet_equilibria(A, W, M);
-        for (int p = 0; p < A.npop; ++p) f[p * nodes + i] = (T)M[p];
+        double W[m], M[NPOP];
+#pragma unroll
+        for (int v = 0; v < m; ++v) W[v] = W0[v * nodes + i];
+        tet_equilibria<SYS, VS>(A, W, M);
+#pragma unroll
+        for (int p = 0; p < NPOP; ++p) f[p * nodes + i] = (T)M[p];
     }
 }
+
+// Launch a (system, velocity set, precision) instance of a pointwise kernel.
+template <template <int, int, typename> class K, typename... Args>
+static cudaError_t tet_dispatch(const TetArgs& a, int prec, unsigned grid, cudaStream_t st, Args... args)
+{
+    auto go = [&](auto sys, auto vs) {
+        constexpr int S = decltype(sys)::value, V = decltype(vs)::value;
+        if (prec == 1) K<S, V, float>::launch(a, grid, st, args...);
+        else K<S, V, double>::launch(a, grid, st, args...);
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    const bool d3q4 = a.velset == 1;
+    switch (a.system) {
+    case kAdvection: d3q4 ? go(I0{}, I1{}) : go(I0{}, I0{}); break;
+    case kEuler: d3q4 ? go(I1{}, I1{}) : go(I1{}, I0{}); break;
+    default: d3q4 ? go(I2{}, I1{}) : go(I2{}, I0{}); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int S, int V, typename T>
+struct RelaxLaunch {
+    static void launch(const TetArgs& a, unsigned grid, cudaStream_t st, const void* star)
+    {
+        tet_relax_kernel<S, V, T><<<grid, 256, 0, st>>>(a, static_cast<const T*>(star));
+    }
+};
+
+template <int S, int V, typename T>
+struct InitLaunch {
+    static void launch(const TetArgs& a, unsigned grid, cudaStream_t st, const double* W)
+    {
+        tet_init_kernel<S, V, T><<<grid, 256, 0, st>>>(a, W);
+    }
+};
 
 cudaError_t tet_launch_setup(const TetSetupArgs& a, cudaStream_t st)
 {
@@ -327,17 +417,13 @@ cudaError_t tet_launch_sweep(const TetArgs& a, const void* prev, void* cur, int 
 cudaError_t tet_launch_relax(const TetArgs& a, const void* star, int prec, cudaStream_t st)
 {
     const unsigned grid = (unsigned)std::min<long long>((a.nodes + 255) / 256, 152LL * 8);
-    if (prec == 1) tet_relax_kernel<float><<<grid, 256, 0, st>>>(a, static_cast<const float*>(star));
-    else tet_relax_kernel<double><<<grid, 256, 0, st>>>(a, static_cast<const double*>(star));
-    return cudaGetLastError();
+    return tet_dispatch<RelaxLaunch>(a, prec, grid, st, star);
 }
 
 cudaError_t tet_launch_init(const TetArgs& a, const double* W, int prec, cudaStream_t st)
 {
     const unsigned grid = (unsigned)std::min<long long>((a.nodes + 255) / 256, 152LL * 8);
-    if (prec == 1) tet_init_kernel<float><<<grid, 256, 0, st>>>(a, W);
-    else tet_init_kernel<double><<<grid, 256, 0, st>>>(a, W);
-    return cudaGetLastError();
+    return tet_dispatch<InitLaunch>(a, prec, grid, st, W);
 }
 
 }  // namespace kin
