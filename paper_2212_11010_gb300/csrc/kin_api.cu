@@ -1044,7 +1044,12 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
     ALLOC(xyz_d, sizeof(double) * 12 * (size_t)n);
     ALLOC(ft_d, ftype.size());
     ALLOC(c64_d, sizeof(double) * (size_t)c->nvel * n * kTetRec);
+    int* rank_d = nullptr;
+    ALLOC(rank_d, sizeof(int) * (size_t)c->nvel * n);
 #undef ALLOC
+    std::vector<int> rank((size_t)c->nvel * n);
+    for (int k = 0; k < c->nvel; ++k)
+        for (int q = 0; q < n; ++q) rank[(size_t)k * n + order[(size_t)k * n + q]] = q;
     cudaError_t e = cudaMemcpyAsync(c->torder, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->tlstart, lstart.data(), sizeof(int) * lstart.size(), cudaMemcpyHostToDevice, c->stream);
@@ -1057,6 +1062,8 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(xyz_d, mesh->xyz, sizeof(double) * 12 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ft_d, ftype.data(), ftype.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rank_d, rank.data(), sizeof(int) * rank.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->errword, 0, sizeof(int) * 4, c->stream);
     if (e == cudaSuccess) {
         TetSetupArgs sa;
@@ -1068,6 +1075,7 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
             for (int i = 0; i < 3; ++i) sa.vel[k][i] = vel[k][i];
         sa.dt = dt;
         sa.ftype = ft_d;
+        sa.rank = rank_d;
         sa.c64 = c64_d;
         sa.c32 = c->esize == 4 ? (float*)c->tcoef : nullptr;
         e = tet_launch_setup(sa, c->stream);
@@ -1083,8 +1091,8 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
         delete c;
         return KIN_ECUDA;
     }
-    // the set-up scratch goes back (the last three allocations)
-    for (int i = 0; i < 3; ++i) {
+    // the set-up scratch goes back (the last four allocations)
+    for (int i = 0; i < 4; ++i) {
         auto b = c->blocks.back();
         if (c->dealloc) c->dealloc(b.first, b.second, (void*)c->stream, c->alloc_user);
         else cudaFree(b.first);
@@ -1092,7 +1100,7 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
         c->blocks.pop_back();
     }
     c->grid = (int)(c->nsub * c->nvel);
-    c->threads = 128;
+    c->threads = kTetSweepThreads;
     *out = c;
     return KIN_OK;
 }

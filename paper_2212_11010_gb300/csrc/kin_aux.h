@@ -85,6 +85,7 @@ cudaError_t sx_launch_init(const SxArgs& a, const double* W, int prec, cudaStrea
 
 // ---- tetrahedral meshes (kin_tet.cu) ----
 constexpr int kTetRec = 24;       // coefficient slots per (velocity, cell)
+constexpr int kTetSweepThreads = 512;
 
 struct TetSetupArgs {
     int ncells, nvel;
@@ -92,14 +93,15 @@ struct TetSetupArgs {
     double vel[6][3];             // V_k
     double dt;
     const unsigned char* ftype;   // [velocity][cell]: 2 bits per face a: 1 inflow, 2 outflow, 0 parallel
-    double* c64;                  // [velocity][cell][kTetRec] FP64 records
+    const int* rank;              // [velocity][cell]: the cell's position in the velocity's level order
+    double* c64;                  // [velocity][position][kTetRec] FP64 records, in level order
     float* c32;                   // FP32 copy (NULL for FP64)
 };
 
 struct TetArgs {
     int ncells, nvel, m, npop, nsub, system, velset;
     long long nodes;              // 4 ncells
-    const void* coef;             // T records [velocity][cell][kTetRec]
+    const void* coef;             // T records [velocity][position in order][kTetRec]
     const int* order;             // [velocity][ncells]: cells by subdomain, then breadth-first
     const int* lstart;            // [velocity][nsub + 1]: first level index of each subdomain in bounds
     const int* bounds;            // level l of the order holds positions [bounds[l], bounds[l + 1])

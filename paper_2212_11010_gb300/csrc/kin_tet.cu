@@ -18,8 +18,8 @@
 // and inside every subdomain sorts the cells breadth-first into levels
 // (cells of one level have no upwind neighbour in the same level).  A step
 // is K launches of the sweep kernel -- one block per (subdomain, velocity),
-// walking the levels with a barrier between them, every thread one cell of
-// the level for all m variables -- and one pointwise launch for the
+// walking the levels with a barrier between them, every thread one (cell,
+// variable) pair of the level -- and one pointwise launch for the
 // Crank-Nicolson extrapolation and the relaxation.  Iteration p reads the
 // neighbour's iterate p-1 across a subdomain interface (a face to another
 // subdomain, or across the periodic boundary) and the current iterate
@@ -117,14 +117,16 @@ __global__ void tet_setup_kernel(TetSetupArgs A)
             for (int j = 0; j < 8; ++j) M[r][j] -= l * M[col][j];
         }
     }
-    double* rec = A.c64 + ((size_t)k * A.ncells + c) * kTetRec;
+    // records in the velocity's level order: a level reads consecutive records
+    const size_t pos = (size_t)A.rank[(size_t)k * A.ncells + c];
+    double* rec = A.c64 + ((size_t)k * A.ncells + pos) * kTetRec;
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) rec[i * 4 + j] = M[i][4 + j];
     rec[16] = vol / 20.0;
     for (int a = 0; a < 4; ++a) rec[17 + a] = cin[a];
     for (int q = 21; q < kTetRec; ++q) rec[q] = 0.0;
     if (A.c32) {
-        float* r32 = A.c32 + ((size_t)k * A.ncells + c) * kTetRec;
+        float* r32 = A.c32 + ((size_t)k * A.ncells + pos) * kTetRec;
         for (int q = 0; q < kTetRec; ++q) r32[q] = (float)rec[q];
     }
 }
@@ -169,7 +171,7 @@ __device__ __forceinline__ void store4(T* p, const T (&u)[4])
 // of a cell read the same coefficient record (one broadcast), and a level of
 // c cells offers c m independent solves.
 template <typename T>
-__global__ void __launch_bounds__(128) tet_sweep_kernel(TetArgs A, const T* __restrict__ prev, T* cur)
+__global__ void __launch_bounds__(kTetSweepThreads) tet_sweep_kernel(TetArgs A, const T* __restrict__ prev, T* cur)
 {
     const int s = blockIdx.x, k = blockIdx.y;
     const int* __restrict__ order = A.order + (size_t)k * A.ncells;
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(128) tet_sweep_kernel(TetArgs A, const T* __re
         for (int it = threadIdx.x; it < items; it += blockDim.x) {
             const int q = it / m, v = it - q * m;
             const int c = order[p0 + q];
-            const T* rec = coef + (size_t)c * kTetRec;
+            const T* rec = coef + (size_t)(p0 + q) * kTetRec;
             const long long pop = (long long)(k * m + v) * nodes;
             T u[4];
             load4(fn + pop + (size_t)c * 4, u);
@@ -408,9 +410,11 @@ cudaError_t tet_launch_sweep(const TetArgs& a, const void* prev, void* cur, int 
 {
     const dim3 grid(a.nsub, a.nvel);
     if (prec == 1)
-        tet_sweep_kernel<float><<<grid, 128, 0, st>>>(a, static_cast<const float*>(prev), static_cast<float*>(cur));
+        tet_sweep_kernel<float><<<grid, kTetSweepThreads, 0, st>>>(a, static_cast<const float*>(prev),
+                                                                  static_cast<float*>(cur));
     else
-        tet_sweep_kernel<double><<<grid, 128, 0, st>>>(a, static_cast<const double*>(prev), static_cast<double*>(cur));
+        tet_sweep_kernel<double><<<grid, kTetSweepThreads, 0, st>>>(a, static_cast<const double*>(prev),
+                                                                   static_cast<double*>(cur));
     return cudaGetLastError();
 }
 
