@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cmath>
+#include <climits>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -62,11 +63,11 @@ struct kin_ctx {
     bool simplex = false;
     int vsgn[4][3] = {};
     double minv[16] = {};
-    void* sxcoef = nullptr;
     double* sxc64 = nullptr;
     double* sxwork = nullptr;
     void* sxtr[2][3] = {};
-    size_t sx_smem = 0;
+    std::vector<double> sx_hrec;      // FP64 records [velocity][sx_stride], passed in the sweep parameters
+    SxPlan sx_plan = {};
     int sx_stride = 0;
     // tetrahedral meshes
     bool tet = false;
@@ -427,7 +428,6 @@ static SxArgs sx_args(const kin_ctx* c)
     SxArgs S;
     memset(&S, 0, sizeof S);
     S.f = c->f;
-    S.coef = c->sxcoef;
     S.nodes = (long long)c->nodes;
     long long tn = 1;
     for (int a = 1; a < c->dim; ++a) tn *= c->NP;
@@ -447,7 +447,6 @@ static SxArgs sx_args(const kin_ctx* c)
     S.nvel = c->nvel;
     S.npop = c->npop;
     S.system = c->system;
-    S.coef_stride = c->sx_stride;
     S.omega = c->omega;
     S.gamma = c->gamma;
     for (int i = 0; i < 16; ++i) S.minv[i] = c->minv[i];
@@ -459,20 +458,25 @@ static SxArgs sx_args(const kin_ctx* c)
     return S;
 }
 
-// One step S(dt) for a d + 1 velocity set: trace pass, K sweeps, relaxation.
+// One step S(dt) for a d + 1 velocity set: K sweeps, then the relaxation.
+// Iterate 1 reads its interface inflow from f^n directly; with K = 1 the
+// sweep writes f^{n+1} in place, so a trace pass copies iterate 0 first.
 static kin_status sx_step(kin_ctx* c)
 {
     SxArgs S = sx_args(c);
     const int prec = c->precision == KIN_FP32;
-    for (int a = 0; a < 3; ++a) S.tr_out[a] = c->sxtr[0][a];
-    KIN_CUDA(c, sx_launch_trace0(S, prec, c->stream));
+    if (c->iters == 1) {
+        for (int a = 0; a < 3; ++a) S.tr_out[a] = c->sxtr[0][a];
+        KIN_CUDA(c, sx_launch_trace0(S, prec, c->stream));
+    }
     for (int it = 1; it <= c->iters; ++it) {
         for (int a = 0; a < 3; ++a) {
             S.tr_in[a] = c->sxtr[(it - 1) & 1][a];
             S.tr_out[a] = c->sxtr[it & 1][a];
         }
+        S.from_f = it == 1 && c->iters > 1;
         S.final_iter = it == c->iters;
-        KIN_CUDA(c, sx_launch_sweep(S, prec, c->sx_smem, c->stream));
+        KIN_CUDA(c, sx_launch_sweep(S, prec, c->sx_hrec.data(), c->sx_stride, c->sx_plan, c->stream));
     }
     KIN_CUDA(c, sx_launch_relax(S, prec, c->stream));
     return KIN_OK;
@@ -637,23 +641,20 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
             for (int a = 0; a < 3; ++a) c->vsgn[k][a] = c->dim == 2 ? s2[k][a] : s3[k][a];
         size_t tn = 1;
         for (int a = 1; a < c->dim; ++a) tn *= c->NP;
-        c->sx_stride = c->NN * c->NN + c->dim * c->NN * (int)tn;
-        c->sx_smem = ((size_t)c->L[0] * c->L[1] * c->L[2] * c->NN + c->sx_stride) * c->esize;
-        if (c->sx_smem > 227 * 1024) {
-            const size_t need = c->sx_smem;
+        c->sx_stride = c->NN * c->NN + c->NN + c->dim * (int)tn;
+        // sweep lanes: the columns of a subdomain along its stepping axis
+        if (c->cells > (size_t)INT_MAX || !sx_sweep_shape(sx_args(c), c->precision == KIN_FP32, &c->sx_plan)) {
+            const int lanes = c->dim == 2 ? std::max(c->L[0], c->L[1]) : c->L[0] * c->L[1];
             delete c;
             return fail(nullptr, KIN_EINVAL,
-                        "a subdomain of one population needs %zu bytes of shared memory (> 227 KB); use more tiles",
-                        need);
+                        "a subdomain has %d columns along its sweep axis: at most 1024, whose sweep state fits "
+                        "227 KB of shared memory (and at most 2^31 - 1 cells); use more tiles", lanes);
         }
         for (int a = 0; a < 3; ++a) {
             c->B[a] = c->L[a];
             c->nblk[a] = c->tiles[a];
             c->nb[a] = 1;
         }
-        c->grid = c->npop * c->tiles[0] * c->tiles[1] * c->tiles[2];
-        c->threads = kSxThreads;
-        c->smem = (int)c->sx_smem;
         kin_status st;
         void* p;
 #define ALLOC(dst, bytes)                                                 \
@@ -672,7 +673,6 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
             for (int a = 0; a < c->dim; ++a)
                 ALLOC(c->sxtr[i][a], (size_t)c->npop * c->tiles[a] * (c->cells / c->n[a]) * tn * c->esize);
         ALLOC(c->sxc64, sizeof(double) * 4 * c->sx_stride);
-        ALLOC(c->sxcoef, c->esize == 4 ? sizeof(float) * 4 * c->sx_stride : 16);
         ALLOC(c->sxwork, sizeof(double) * 4 * 2 * kSxMaxNN * kSxMaxNN);
         ALLOC(c->c64, sizeof(double) * 6 * kCoefStride);
         ALLOC(c->gll, sizeof(double) * 2 * kMaxNP);
@@ -681,7 +681,6 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
         ALLOC(c->result, sizeof(double) * 16);
         ALLOC(c->errword, sizeof(int) * 4);
 #undef ALLOC
-        if (c->esize == 8) c->sxcoef = c->sxc64;
         SetupArgs sa;
         memset(&sa, 0, sizeof sa);
         sa.dim = c->dim;
@@ -703,7 +702,6 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
         for (int a = 0; a < 3; ++a) xa.h[a] = c->h[a];
         xa.stride = c->sx_stride;
         xa.c64 = c->sxc64;
-        xa.c32 = c->esize == 4 ? (float*)c->sxcoef : nullptr;
         xa.minv = c->result;
         xa.work = c->sxwork;
         cudaError_t e = cudaMemsetAsync(c->errword, 0, sizeof(int) * 4, c->stream);
@@ -711,7 +709,17 @@ kin_status kin_create(const kin_mesh* mesh, const kin_model* model, int degree, 
         if (e == cudaSuccess) e = sx_launch_setup(xa, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(c->minv, c->result, sizeof(double) * 16, cudaMemcpyDeviceToHost, c->stream);
+        c->sx_hrec.assign((size_t)c->nvel * c->sx_stride, 0.0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->sx_hrec.data(), c->sxc64, sizeof(double) * c->nvel * c->sx_stride,
+                                cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) {
+            e = sx_sweep_plan(sx_args(c), c->precision == KIN_FP32, &c->sx_plan);
+            c->grid = c->sx_plan.split ? c->sx_plan.bpv : c->nvel * c->sx_plan.bpv;
+            c->threads = c->sx_plan.threads;
+            c->smem = (int)c->sx_plan.smem;
+        }
         if (e != cudaSuccess) {
             g_create_error = std::string("setup failed: ") + cudaGetErrorString(e);
             release_all(c);

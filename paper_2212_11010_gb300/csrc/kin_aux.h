@@ -46,7 +46,6 @@ typedef void (*StepKernel)(Inst);
 
 // ---- d + 1 velocity sets (kin_simplex.cu) ----
 constexpr int kSxMaxNN = 27;      // (p+1)^d <= 27 (3D p <= 2, 2D p <= 3)
-constexpr int kSxThreads = 64;
 
 struct SxSetupArgs {
     int dim, degree;
@@ -54,14 +53,12 @@ struct SxSetupArgs {
     double h[3];
     int stride;          // elements per velocity record
     double* c64;         // [d+1][stride] FP64 records
-    float* c32;          // FP32 copy (NULL for FP64)
     double* minv;        // [(d+1)^2] inverse moment matrix
     double* work;        // [(d+1)][2 kSxMaxNN^2] scratch
 };
 
 struct SxArgs {
     void* f;
-    const void* coef;             // T records of sx_setup_kernel
     const void* tr_in[3];         // per axis: [pop][NS_a][glines_a]
     void* tr_out[3];
     long long nodes;
@@ -70,7 +67,7 @@ struct SxArgs {
     int n[3], L[3], NS[3];
     int vsgn[4][3];               // sign of V_k along each axis (+1, -1, 0)
     int dim, degree, nn, m, nvel, npop, system;
-    int coef_stride;
+    int from_f;                   // iterate 1: interface inflow is f^n of the upwind cell
     int final_iter;
     double omega, gamma;
     double adv[3];
@@ -79,7 +76,17 @@ struct SxArgs {
 
 cudaError_t sx_launch_setup(const SxSetupArgs& a, cudaStream_t st);
 cudaError_t sx_launch_trace0(const SxArgs& a, int prec, cudaStream_t st);
-cudaError_t sx_launch_sweep(const SxArgs& a, int prec, size_t smem, cudaStream_t st);
+// Launch plan of a sweep: threads per block (the subdomain's columns rounded
+// to warps), dynamic shared memory, blocks per velocity, one launch per
+// velocity (split) or one for all.
+struct SxPlan {
+    int threads, bpv, split, occupancy;
+    size_t smem;
+};
+int sx_sweep_shape(const SxArgs& a, int prec, SxPlan* plan);   // host only: 0 if no shape fits
+cudaError_t sx_sweep_plan(const SxArgs& a, int prec, SxPlan* plan);
+cudaError_t sx_launch_sweep(const SxArgs& a, int prec, const double* hrec, int rstride, const SxPlan& plan,
+                            cudaStream_t st);
 cudaError_t sx_launch_relax(const SxArgs& a, int prec, cudaStream_t st);
 cudaError_t sx_launch_init(const SxArgs& a, const double* W, int prec, cudaStream_t st);
 

@@ -17,8 +17,10 @@
 //                precomputed in FP64).
 #include "kin_aux.h"
 #include "kin_device.cuh"
+#include "kin_tma.cuh"
 
 #include <math.h>
+#include <string.h>
 
 namespace kin {
 
@@ -72,11 +74,14 @@ __device__ static void sx_gll(int p, double* xi, double* w)
     }
 }
 
-// One thread per velocity.  Record layout (sx_coef_stride elements):
-//   [0, NN*NN)                 Pm = A^{-1} W_cell - I   (row-major)
-//   [NN*NN + a*NN*TN, ...)     G_a = nu_a A^{-1} (e_in,a x W_perp)  (NN x TN)
+// One thread per velocity.  Record layout (NN^2 + NN + d TN elements):
+//   [0, NN*NN)                 A^{-1}   (row-major)
+//   [NN*NN, NN*NN + NN)        W_cell   (tensor Gauss-Lobatto weights)
+//   [NN*NN + NN + a*TN, ...)   nu_a W_perp on the inflow face of axis a (0 if V_a = 0)
 // with A = W_cell + sum_a nu_a (S_a at axis a, W at the others),
-// S_a = Q + e_0 e_0^T (V_a > 0) or -Q + e_p e_p^T (V_a < 0), nu_a = |V_a| dt / (2 h_a).
+// S_a = Q + e_0 e_0^T (V_a > 0) or -Q + e_p e_p^T (V_a < 0), nu_a = |V_a| dt / (2 h_a),
+// so that the CN half step of eq. dg_imp is f* = A^{-1} (W_cell f^n + sum_a nu_a E_a W_perp tr_a),
+// E_a the injection onto the inflow face nodes of axis a.
 // Thread 0 also writes the inverse of the moment matrix [1...1; V_0 ... V_d].
 __global__ void sx_setup_kernel(SxSetupArgs A)
 {
@@ -140,10 +145,8 @@ __global__ void sx_setup_kernel(SxSetupArgs A)
         Dm[i][i] = diag;
     }
     double S[3][kMaxNP][kMaxNP], nu[3];
-    int in_node[3];
     for (int a = 0; a < d; ++a) {
         nu[a] = fabs(V[a]) * 0.5 * A.dt / A.h[a];
-        in_node[a] = V[a] > 0 ? 0 : p;
         for (int i = 0; i < np; ++i)
             for (int j = 0; j < np; ++j) {
                 const double q = w[i] * Dm[i][j];
@@ -202,35 +205,25 @@ __global__ void sx_setup_kernel(SxSetupArgs A)
     }
     double* rec = A.c64 + (size_t)k * A.stride;
     for (int i = 0; i < nn; ++i)
-        for (int j = 0; j < nn; ++j) {
-            int jj[3] = {j % np, (j / np) % np, j / (np * np)};
-            double wj = 1.0;
-            for (int b = 0; b < d; ++b) wj *= w[jj[b]];
-            rec[i * nn + j] = Mx[i * w2 + nn + j] * wj - (i == j ? 1.0 : 0.0);
-        }
-    for (int a = 0; a < d; ++a) {
-        double* G = rec + nn * nn + a * nn * tn;
-        for (int i = 0; i < nn; ++i)
-            for (int t = 0; t < tn; ++t) G[i * tn + t] = 0.0;
-        if (V[a] == 0.0) continue;
-        // inflow face of axis a: nodes with index in_node[a] along a; the
-        // transverse node index t enumerates the other axes (lowest first)
-        for (int j = 0; j < nn; ++j) {
-            int jj[3] = {j % np, (j / np) % np, j / (np * np)};
-            if (jj[a] != in_node[a]) continue;
+        for (int j = 0; j < nn; ++j) rec[i * nn + j] = Mx[i * w2 + nn + j];
+    for (int j = 0; j < nn; ++j) {
+        int jj[3] = {j % np, (j / np) % np, j / (np * np)};
+        double wj = 1.0;
+        for (int b = 0; b < d; ++b) wj *= w[jj[b]];
+        rec[nn * nn + j] = wj;
+    }
+    for (int a = 0; a < d; ++a)
+        for (int t = 0; t < tn; ++t) {
+            // transverse node t enumerates the other axes, lowest first
             double wt = 1.0;
-            int t = 0, mul = 1;
+            int r = t;
             for (int b = 0; b < d; ++b) {
                 if (b == a) continue;
-                wt *= w[jj[b]];
-                t += jj[b] * mul;
-                mul *= np;
+                wt *= w[r % np];
+                r /= np;
             }
-            for (int i = 0; i < nn; ++i) G[i * tn + t] += nu[a] * Mx[i * w2 + nn + j] * wt;
+            rec[nn * nn + nn + a * tn + t] = V[a] == 0.0 ? 0.0 : nu[a] * wt;
         }
-    }
-    if (A.c32)
-        for (int e = 0; e < A.stride; ++e) A.c32[(size_t)k * A.stride + e] = (float)rec[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -319,158 +312,454 @@ __global__ void sx_trace0_kernel(SxArgs S)
     }
 }
 
-// One (population, subdomain) per thread block: wavefront sweep of iterate p.
-template <int D, int P, typename T>
-__global__ void __launch_bounds__(kSxThreads) sx_sweep_kernel(SxArgs S)
+// Sign of V_k along axis a for the d + 1 sets (D2Q3: 0, 120 and 240 degrees;
+// D3Q4: the cube diagonals (1,1,1), (1,-1,-1), (-1,1,-1), (-1,-1,1)).
+__host__ __device__ constexpr int sx_sign(int D, int k, int a)
 {
-    constexpr int NP = P + 1;
-    constexpr int NN = ipow(NP, D);
-    constexpr int TN = ipow(NP, D - 1);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);             // L0 L1 L2 cells x NN
-    T* cf = tile + (size_t)S.L[0] * S.L[1] * S.L[2] * NN;  // coefficients of this velocity
+    if (D == 2) {
+        if (a == 0) return k == 0 ? 1 : -1;
+        if (a == 1) return k == 0 ? 0 : (k == 1 ? 1 : -1);
+        return 0;
+    }
+    if (a == 0) return k < 2 ? 1 : -1;
+    if (a == 1) return (k == 0 || k == 2) ? 1 : -1;
+    if (a == 2) return (k == 0 || k == 3) ? 1 : -1;
+    return 0;
+}
+
+// Cell node with index ja along axis a and transverse node tt (the other
+// axes, lowest first); node = j0 + NP j1 + NP^2 j2.
+template <int D, int NP>
+__host__ __device__ constexpr int sx_node(int a, int ja, int tt)
+{
+    int j[3] = {0, 0, 0};
+    int r = tt;
+    for (int b = 0; b < D; ++b) {
+        if (b == a) continue;
+        j[b] = r % NP;
+        r /= NP;
+    }
+    j[a] = ja;
+    return j[0] + NP * j[1] + NP * NP * j[2];
+}
+
+// Division by an invariant divisor d >= 1 for dividends below 2^31
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, the round-up multiplier): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, q = (mulhi(m, n) + n) >> l.
+struct SxDiv {
+    unsigned m;
+    int l;
+};
+
+static inline SxDiv sx_div_make(int d)
+{
+    SxDiv r;
+    int l = 0;
+    while ((1LL << l) < d) ++l;
+    r.l = l;
+    r.m = (unsigned)((((1ULL << 32) * ((1ULL << l) - (unsigned long long)d)) / (unsigned long long)d) + 1);
+    return r;
+}
+
+__device__ __forceinline__ int sx_div(int n, SxDiv d)
+{
+    return (int)(((unsigned long long)__umulhi(d.m, (unsigned)n) + (unsigned)n) >> d.l);
+}
+
+// Launch parameters of one sweep.  The block inverse, the cell weights and
+// the face weights of every velocity travel in the parameter block, so the
+// fully unrolled cell solve takes them as constant-bank operands.
+template <int D, int P, typename T>
+struct SxWave {
+    static constexpr int NP = P + 1, NN = ipow(NP, D), TN = ipow(NP, D - 1), NV = D + 1;
+    SxArgs S;
+    int bpv;            // thread blocks per velocity
+    int k0;             // first velocity of this launch
+    SxDiv div_nsub, div_ns0, div_ns1;
+    T ainv[NV][NN * NN];
+    T wcell[NN];
+    T face[NV][D][TN];
+};
+
+// Prefetch rings of the sweep, filled by cp.async kSxRing - 1 waves ahead:
+// per lane and wave, the cell's f^n (NN values) and its interface inflow
+// along the stepping axis (TN values); per wave and boundary lane of a
+// transverse axis, that axis' interface inflow (TN values).  Each lane owns
+// NEP contiguous elements per variable and slot (NEP = NN + TN rounded up so
+// that NEP / CW is odd: lanes then fall in distinct banks for scalar (CW = 1)
+// and 16-byte (CW > 1) accesses).  The exchange of outflow faces between
+// lanes uses the same rule with TN.
+__host__ __device__ constexpr int sx_pad_odd(int n, int cw)
+{
+    return ((n + cw - 1) / cw) % 2 ? (n + cw - 1) / cw * cw : ((n + cw - 1) / cw + 1) * cw;
+}
+
+template <int D, int P, typename T>
+struct SxRing {
+    static constexpr int NN = ipow(P + 1, D), TN = ipow(P + 1, D - 1);
+    static constexpr int C = 16 / (int)sizeof(T);
+    static constexpr int CW = (NN % C == 0 && TN % C == 0) ? C : 1;
+    static constexpr int NEP = sx_pad_odd(NN + TN, CW);   // f^n of the cell + inflow along DEP
+    static constexpr int TNP = sx_pad_odd(TN, CW);
+};
+constexpr int kSxRing = 2;            // slots; waves in flight = kSxRing - 1
+
+// Position of one lane in the stream of problems: q counts the lane's cells
+// (q = wave - skew), od is the oriented coordinate along the stepping axis.
+struct SxTrack {
+    int q, od, i, pop;
+    int s[3], g[3];
+    bool valid;
+};
+
+template <int NN, typename T>
+__device__ __forceinline__ void sx_st(T* p, const T* u)
+{
+    if constexpr ((NN * sizeof(T)) % 16 == 0) {
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int k = 0; k < NN / 4; ++k)
+                reinterpret_cast<float4*>(p)[k] = make_float4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NN / 2; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(u[2 * k], u[2 * k + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NN; ++i) p[i] = u[i];
+    }
+}
+
+// N values from / to shared memory, 16 bytes at a time when VEC (the address
+// is then 16-byte aligned and N a multiple of 16 / sizeof(T)).
+template <int N, bool VEC, typename T>
+__device__ __forceinline__ void sx_lds(const T* p, T* v)
+{
+    if constexpr (VEC && sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k) {
+            const float4 q = reinterpret_cast<const float4*>(p)[k];
+            v[4 * k] = q.x;
+            v[4 * k + 1] = q.y;
+            v[4 * k + 2] = q.z;
+            v[4 * k + 3] = q.w;
+        }
+    } else if constexpr (VEC) {
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) {
+            const double2 q = reinterpret_cast<const double2*>(p)[k];
+            v[2 * k] = q.x;
+            v[2 * k + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = p[i];
+    }
+}
+
+template <int N, bool VEC, typename T>
+__device__ __forceinline__ void sx_sts(T* p, const T* v)
+{
+    if constexpr (VEC && sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k)
+            reinterpret_cast<float4*>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else if constexpr (VEC) {
+#pragma unroll
+        for (int k = 0; k < N / 2; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) p[i] = v[i];
+    }
+}
+
+// Transverse cell id of the face of axis a (the other axes, lowest first).
+template <int D>
+__device__ __forceinline__ int sx_face_cell(const SxArgs& S, int a, const int g[3])
+{
+    if (D == 2) return a == 0 ? g[1] : g[0];
+    const int b1 = a == 0 ? 1 : 0, b2 = a == 2 ? 1 : 2;
+    return g[b2] * S.n[b1] + g[b1];
+}
+
+template <int D, int KV>
+__device__ __forceinline__ constexpr int sx_sg(int a)
+{
+    return a == 0 ? sx_sign(D, KV, 0) : (a == 1 ? sx_sign(D, KV, 1) : sx_sign(D, KV, 2));
+}
+
+// One velocity's part of a sweep (iterate it of eq. ibvp).  A thread block
+// streams the problems (variable, subdomain) lb, lb + bpv, ... of velocity
+// KV.  Its lanes are the subdomain's columns along the stepping axis DEP (the last axis with
+// V_a != 0), indexed by the oriented transverse coordinates; lane o visits
+// its column's cells one per wave, delayed by skew = sum of its oriented
+// transverse coordinates, so that at every wave the cell of each lane has its
+// upwind neighbours (Sec. 3.2) already done: along DEP the lane's own previous
+// cell, along a transverse axis the previous wave of the neighbouring lane,
+// which passes its outflow face through shared memory.  Consecutive
+// problems follow each other in the column without a gap, so every lane is
+// busy except during the first and last skew waves.  Cells on a subdomain's
+// upwind boundary take their inflow from the previous iterate's traces (from
+// f^n itself on iterate 1); cells on its downwind boundary write this
+// iterate's traces.  The cell solve is the CN half step of eq. dg_imp in
+// shifted form: with t = f^n at node 0,
+//   f* = t + A^{-1} (W_cell (f^n - t) + sum_a nu_a E_a W_perp (tr_a - t)),
+// which keeps constant states exactly.  The last iterate writes
+// f^{n+1} = 2 f* - f^n in place.
+template <int D, int P, int KV, typename T>
+__device__ __forceinline__ void sx_sweep_velocity(const SxWave<D, P, T>& A, const int lb, T* xs, T* ring)
+{
+    constexpr int NP = P + 1, NN = ipow(NP, D), TN = ipow(NP, D - 1);
+    using RG = SxRing<D, P, T>;
+    constexpr int CW = RG::CW, NEP = RG::NEP, TNP = RG::TNP;
+    constexpr int PF = kSxRing - 1;
+    constexpr int DEP = D == 3 ? 2 : (KV == 0 ? 0 : 1);
+    constexpr int TA0 = D == 3 ? 0 : 1 - DEP;
+    constexpr int TA1 = D == 3 ? 1 : 0;          // only used when D == 3
+    constexpr bool X0 = sx_sign(D, KV, TA0) != 0;
+    constexpr bool X1 = D == 3 && sx_sign(D, KV, TA1) != 0;
+    constexpr int SGD = sx_sign(D, KV, DEP);
+    // node 0 receives face inflow iff some axis enters at index 0
+    constexpr bool R0 = sx_sign(D, KV, 0) > 0 || sx_sign(D, KV, 1) > 0 || sx_sign(D, KV, 2) > 0;
+
+    const SxArgs& S = A.S;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n0 = S.L[TA0], n1 = D == 3 ? S.L[TA1] : 1;
+    const int Ld = S.L[DEP];
+    const bool active = tid < n0 * n1;
+    const int ot1 = D == 3 ? tid / n0 : 0, ot0 = tid - ot1 * n0;
+    const int lt0 = sx_sign(D, KV, TA0) < 0 ? n0 - 1 - ot0 : ot0;
+    const int lt1 = (D == 3 && sx_sign(D, KV, TA1) < 0) ? n1 - 1 - ot1 : ot1;
+    const int skew = (X0 ? ot0 : 0) + (X1 ? ot1 : 0);
+    const int maxskew = (X0 ? n0 - 1 : 0) + (X1 ? n1 - 1 : 0);
     const int nsub = S.NS[0] * S.NS[1] * S.NS[2];
-    const int pop = blockIdx.x / nsub, sub = blockIdx.x % nsub;
-    const int k = pop / S.m;
-    const int s[3] = {sub % S.NS[0], (sub / S.NS[0]) % S.NS[1], sub / (S.NS[0] * S.NS[1])};
-    const int L0 = S.L[0], L1 = S.L[1], L2 = S.L[2];
-    const int org[3] = {s[0] * L0, s[1] * L1, s[2] * L2};
+    const int nprob = S.m * nsub;                // (variable, subdomain)
+    const int nb = lb < nprob ? (nprob - lb + A.bpv - 1) / A.bpv : 0;
+    const int span = nb * Ld;
+    const int total = nb > 0 ? span + maxskew : 0;
     T* f = static_cast<T*>(S.f);
-    const long long fbase = (long long)pop * S.nodes;
-    const int tid = threadIdx.x, nth = blockDim.x;
 
-    // load the subdomain (rows of L0 cells are contiguous) and the coefficients
-    const int rowlen = L0 * NN, nrows = L1 * L2;
-    for (int idx = tid; idx < nrows * rowlen; idx += nth) {
-        const int row = idx / rowlen, e = idx - (idx / rowlen) * rowlen;
-        const int ly = row % L1, lz = row / L1;
-        const long long g = fbase + (((long long)(org[2] + lz) * S.n[1] + (org[1] + ly)) * S.n[0] + org[0]) * NN + e;
-        tile[idx] = f[g];
-    }
-    const T* crec = static_cast<const T*>(S.coef) + (size_t)k * S.coef_stride;
-    for (int e = tid; e < S.coef_stride; e += nth) cf[e] = crec[e];
-    __syncthreads();
+    auto advance = [&](SxTrack& t) {
+        ++t.q;
+        t.valid = false;
+        if (t.q < 0 || t.q >= span) return;
+        bool fresh = false;
+        if (t.q == 0) {
+            t.od = 0;
+            t.i = 0;
+            fresh = true;
+        } else if (++t.od == Ld) {
+            t.od = 0;
+            ++t.i;
+            fresh = true;
+        }
+        if (fresh) {
+            const int pid = lb + t.i * A.bpv;
+            const int v = sx_div(pid, A.div_nsub), s = pid - v * nsub;
+            const int s12 = sx_div(s, A.div_ns0), s2 = sx_div(s12, A.div_ns1);
+            t.pop = KV * S.m + v;
+            t.s[0] = s - s12 * S.NS[0];
+            t.s[1] = s12 - s2 * S.NS[1];
+            t.s[2] = s2;
+            t.g[TA0] = t.s[TA0] * S.L[TA0] + lt0;
+            if (D == 3) t.g[TA1] = t.s[TA1] * S.L[TA1] + lt1;
+            else t.g[2] = 0;
+        }
+        t.g[DEP] = t.s[DEP] * Ld + (SGD < 0 ? Ld - 1 - t.od : t.od);
+        t.valid = active;
+    };
 
-    const int* sg = S.vsgn[k];
-    // wavefront structure: the dependent axis is the last one with V_a != 0
-    int dep = 0;
-    for (int a = 0; a < D; ++a)
-        if (sg[a] != 0) dep = a;
-    int nwave = 1, ncand = 1;
-    for (int a = 0; a < D; ++a) {
-        if (sg[a] != 0) nwave += S.L[a] - 1;
-        if (a != dep) ncand *= S.L[a];
-    }
-    for (int wv = 0; wv < nwave; ++wv) {
-        for (int cand = tid; cand < ncand; cand += nth) {
-            // oriented coordinates of the non-dependent axes, then the dependent one
-            int o[3] = {0, 0, 0}, rem = cand, sumo = 0;
-            for (int a = 0; a < D; ++a) {
-                if (a == dep) continue;
-                o[a] = rem % S.L[a];
-                rem /= S.L[a];
-                if (sg[a] != 0) sumo += o[a];
+    // interface inflow is needed on the upwind boundary of the subdomain
+    auto at_inflow = [&](const SxTrack& t, int a) {
+        return a == DEP ? t.od == 0 : (a == TA0 ? ot0 == 0 : ot1 == 0);
+    };
+    auto at_outflow = [&](const SxTrack& t, int a) {
+        return a == DEP ? t.od == Ld - 1 : (a == TA0 ? ot0 == n0 - 1 : ot1 == n1 - 1);
+    };
+    // this lane's elements in ring slot r
+    auto slot = [&](int r) -> T* { return ring + (r * nt + tid) * NEP; };
+    // transverse inflow of boundary lane b of axis ax in slot r
+    T* tring = ring + kSxRing * nt * NEP;
+    const int nbm = D == 2 ? 1 : (n0 > n1 ? n0 : n1);
+    auto tslot = [&](int r, int ax, int b) -> T* { return tring + ((r * 2 + ax) * nbm + b) * TNP; };
+    const int bidx0 = ot1, bidx1 = ot0;          // boundary index of this lane on TA0 / TA1
+    // exchange [parity][axis][lane][TNP]
+    auto xslot = [&](int par, int ax) -> T* { return xs + ((par * 2 + ax) * nt + tid) * TNP; };
+
+    // issue the copies of the wave tracked by t into ring slot r
+    auto fetch = [&](const SxTrack& t, int r) {
+        if (t.valid) {
+            T* dst = slot(r);
+            const int cell = (t.g[2] * S.n[1] + t.g[1]) * S.n[0] + t.g[0];
+            const T* src = f + (long long)t.pop * S.nodes + (long long)cell * NN;
+            if constexpr (CW > 1) {
+#pragma unroll
+                for (int e = 0; e < NN; e += CW) cp16_g2s(dst + e, src + e);
+            } else {
+#pragma unroll
+                for (int e = 0; e < NN; ++e) cp_small_g2s<sizeof(T)>(dst + e, src + e);
             }
-            o[dep] = wv - sumo;
-            if (o[dep] < 0 || o[dep] >= S.L[dep]) continue;
-            int c[3] = {0, 0, 0};
-            for (int a = 0; a < D; ++a) c[a] = sg[a] < 0 ? S.L[a] - 1 - o[a] : o[a];
-            T* cell = tile + ((c[2] * L1 + c[1]) * L0 + c[0]) * NN;
-            T u[NN], dl[NN];
 #pragma unroll
-            for (int i = 0; i < NN; ++i) u[i] = cell[i];
-#pragma unroll
-            for (int i = 0; i < NN; ++i) {
-                T acc = 0;
-#pragma unroll
-                for (int j = 0; j < NN; ++j) acc = fma(cf[i * NN + j], u[j], acc);
-                dl[i] = acc;
-            }
             for (int a = 0; a < D; ++a) {
-                if (sg[a] == 0) continue;
-                const int in_node = sg[a] > 0 ? 0 : NP - 1;     // inflow face node along a
-                const int up_node = sg[a] > 0 ? NP - 1 : 0;     // matching node of the upwind cell
-                T t[TN];
-                if (o[a] > 0) {
-                    int cu[3] = {c[0], c[1], c[2]};
-                    cu[a] -= sg[a];
-                    const T* ucell = tile + ((cu[2] * L1 + cu[1]) * L0 + cu[0]) * NN;
+                const int sg = sx_sg<D, KV>(a);
+                if (sg == 0 || !at_inflow(t, a)) continue;
+                T* dbase = a == DEP ? dst + NN : tslot(r, a == TA0 ? 0 : 1, a == TA0 ? bidx0 : bidx1);
+                if (S.from_f) {
+                    // iterate 0 of eq. ibvp: f^n on the outflow face of the upwind cell
+                    int gu[3] = {t.g[0], t.g[1], t.g[2]};
+                    gu[a] -= sg;
+                    if (gu[a] < 0) gu[a] += S.n[a];
+                    if (gu[a] >= S.n[a]) gu[a] -= S.n[a];
+                    const T* up = f + (long long)t.pop * S.nodes
+                        + (long long)((gu[2] * S.n[1] + gu[1]) * S.n[0] + gu[0]) * NN;
+                    const int out = sg > 0 ? P : 0;
 #pragma unroll
-                    for (int tt = 0; tt < TN; ++tt) {
-                        // transverse node tt -> cell node with index up_node along a
-                        int jn[3] = {0, 0, 0}, r2 = tt;
-                        for (int b = 0; b < D; ++b) {
-                            if (b == a) continue;
-                            jn[b] = r2 % NP;
-                            r2 /= NP;
-                        }
-                        jn[a] = up_node;
-                        t[tt] = ucell[jn[0] + NP * jn[1] + NP * NP * jn[2]];
-                    }
+                    for (int tt = 0; tt < TN; ++tt)
+                        cp_small_g2s<sizeof(T)>(dbase + tt, up + sx_node<D, NP>(a, out, tt));
                 } else {
-                    // across the interface: the upwind subdomain's previous iterate
-                    int sup = s[a] - sg[a];
+                    int sup = t.s[a] - sg;
                     if (sup < 0) sup += S.NS[a];
                     if (sup >= S.NS[a]) sup -= S.NS[a];
-                    const T* tin = static_cast<const T*>(S.tr_in[a]) + (long long)pop * S.NS[a] * S.glines[a]
-                        + (long long)sup * S.glines[a];
-                    int cg[3] = {org[0] + c[0], org[1] + c[1], org[2] + c[2]};
+                    const T* tr = static_cast<const T*>(S.tr_in[a]) + ((long long)t.pop * S.NS[a] + sup) * S.glines[a]
+                        + (long long)sx_face_cell<D>(S, a, t.g) * TN;
+                    if constexpr (CW > 1) {
 #pragma unroll
-                    for (int tt = 0; tt < TN; ++tt) {
-                        int jn[3] = {0, 0, 0}, r2 = tt;
-                        for (int b = 0; b < D; ++b) {
-                            if (b == a) continue;
-                            jn[b] = r2 % NP;
-                            r2 /= NP;
-                        }
-                        t[tt] = tin[sx_gline(S, a, cg, jn, NP)];
+                        for (int tt = 0; tt < TN; tt += CW) cp16_g2s(dbase + tt, tr + tt);
+                    } else {
+#pragma unroll
+                        for (int tt = 0; tt < TN; ++tt) cp_small_g2s<sizeof(T)>(dbase + tt, tr + tt);
                     }
-                    (void)in_node;
                 }
-                const T* G = cf + NN * NN + a * NN * TN;
+            }
+        }
+        cp_commit();
+    };
+
+    T pd[TN];                                   // own outflow face along DEP (previous wave)
 #pragma unroll
-                for (int i = 0; i < NN; ++i)
+    for (int tt = 0; tt < TN; ++tt) pd[tt] = T(0);
+
+    auto compute = [&](int W, const SxTrack& t, int rs) {
+        if (!t.valid) return;
+        const int par = W & 1;
+        const T* sl = slot(rs);
+        // where each axis' inflow comes from: the interface (ring), the own
+        // previous cell (registers) or the upwind lane (exchange)
+        const T* isrc[3] = {nullptr, nullptr, nullptr};
+        bool fromreg[3] = {false, false, false};
 #pragma unroll
-                    for (int tt = 0; tt < TN; ++tt) dl[i] = fma(G[i * TN + tt], t[tt], dl[i]);
+        for (int a = 0; a < D; ++a) {
+            const int sg = sx_sg<D, KV>(a);
+            if (sg == 0) continue;
+            if (a == DEP) {
+                if (at_inflow(t, a)) isrc[a] = sl + NN;
+                else fromreg[a] = true;
+            } else {
+                const int ax = a == TA0 ? 0 : 1;
+                isrc[a] = at_inflow(t, a) ? tslot(rs, ax, ax == 0 ? bidx0 : bidx1)
+                                          : xslot(par ^ 1, ax) - (a == TA0 ? 1 : n0) * TNP;
+            }
+        }
+        T u[NN];
+        sx_lds<NN, (CW > 1)>(sl, u);
+        const T tref = u[0];
+        T r[NN];
+        r[0] = T(0);
+#pragma unroll
+        for (int j = 1; j < NN; ++j) r[j] = A.wcell[j] * (u[j] - tref);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int sg = sx_sg<D, KV>(a);
+            if (sg == 0) continue;
+            const int in = sg > 0 ? 0 : P;
+            T tv[TN];
+            if (a == DEP && fromreg[a]) {
+#pragma unroll
+                for (int tt = 0; tt < TN; ++tt) tv[tt] = pd[tt];
+            } else {
+                sx_lds<TN, (CW > 1)>(isrc[a], tv);
             }
 #pragma unroll
-            for (int i = 0; i < NN; ++i) cell[i] = u[i] + dl[i];      // f* replaces f^n
+            for (int tt = 0; tt < TN; ++tt) {
+                const int j = sx_node<D, NP>(a, in, tt);
+                r[j] = fma(A.face[KV][a][tt], tv[tt] - tref, r[j]);
+            }
         }
+        // x = A^{-1} r by columns: each step is NN independent FMAs
+        T x[NN];
+#pragma unroll
+        for (int i = 0; i < NN; ++i) x[i] = R0 ? A.ainv[KV][i * NN] * r[0] : A.ainv[KV][i * NN + 1] * r[1];
+#pragma unroll
+        for (int j = R0 ? 1 : 2; j < NN; ++j)
+#pragma unroll
+            for (int i = 0; i < NN; ++i) x[i] = fma(A.ainv[KV][i * NN + j], r[j], x[i]);
+#pragma unroll
+        for (int i = 0; i < NN; ++i) x[i] += tref;
+        // outflow faces: transverse ones to the next lanes, DEP kept here
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const int sg = sx_sg<D, KV>(a);
+            if (sg == 0) continue;
+            const int out = sg > 0 ? P : 0;
+            T o[TN];
+#pragma unroll
+            for (int tt = 0; tt < TN; ++tt) o[tt] = x[sx_node<D, NP>(a, out, tt)];
+            if (a == DEP) {
+#pragma unroll
+                for (int tt = 0; tt < TN; ++tt) pd[tt] = o[tt];
+            } else {
+                sx_sts<TN, (CW > 1)>(xslot(par, a == TA0 ? 0 : 1), o);
+            }
+            if (!S.final_iter && at_outflow(t, a)) {
+                T* tr = static_cast<T*>(S.tr_out[a]) + ((long long)t.pop * S.NS[a] + t.s[a]) * S.glines[a]
+                    + (long long)sx_face_cell<D>(S, a, t.g) * TN;
+                sx_st<TN>(tr, o);
+            }
+        }
+        if (S.final_iter) {
+            const int cell = (t.g[2] * S.n[1] + t.g[1]) * S.n[0] + t.g[0];
+#pragma unroll
+            for (int i = 0; i < NN; ++i) x[i] = fma(T(2), x[i], -u[i]);
+            sx_st<NN>(f + (long long)t.pop * S.nodes + (long long)cell * NN, x);
+        }
+    };
+
+    SxTrack tp, tc;
+    tp.q = tc.q = -skew - 1;
+    tp.od = tc.od = tp.i = tc.i = tp.pop = tc.pop = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tp.s[a] = tc.s[a] = tp.g[a] = tc.g[a] = 0;
+    tp.valid = tc.valid = false;
+    for (int k = 0; k < PF; ++k) {
+        advance(tp);
+        fetch(tp, k);
+    }
+    for (int W = 0; W < total; ++W) {
+        advance(tp);
+        fetch(tp, (W + PF) % kSxRing);             // wave W + PF
+        cp_wait_group<PF>();                        // wave W has landed
+        advance(tc);
+        compute(W, tc, W % kSxRing);
         __syncthreads();
     }
+    cp_wait_group<0>();
+}
 
-    // outflow traces of this iterate on the subdomain's downwind faces
-    for (int a = 0; a < D; ++a) {
-        if (sg[a] == 0) continue;
-        int ext[3] = {L0, L1, L2};
-        ext[a] = 1;
-        const int nface = ext[0] * ext[1] * ext[2] * TN;
-        T* tout = static_cast<T*>(S.tr_out[a]) + (long long)pop * S.NS[a] * S.glines[a] + (long long)s[a] * S.glines[a];
-        for (int e = tid; e < nface; e += nth) {
-            const int tt = e % TN, fc = e / TN;
-            int c[3] = {fc % ext[0], (fc / ext[0]) % ext[1], fc / (ext[0] * ext[1])};
-            c[a] = sg[a] > 0 ? S.L[a] - 1 : 0;
-            int jn[3] = {0, 0, 0}, r2 = tt;
-            for (int b = 0; b < D; ++b) {
-                if (b == a) continue;
-                jn[b] = r2 % NP;
-                r2 /= NP;
-            }
-            jn[a] = sg[a] > 0 ? NP - 1 : 0;
-            const T v = tile[((c[2] * L1 + c[1]) * L0 + c[0]) * NN + jn[0] + NP * jn[1] + NP * NP * jn[2]];
-            int cg[3] = {org[0] + c[0], org[1] + c[1], org[2] + c[2]};
-            tout[sx_gline(S, a, cg, jn, NP)] = v;
-        }
-    }
-    // last iterate: f^{n+1} = 2 f* - f^n, in place
-    if (S.final_iter) {
-        for (int idx = tid; idx < nrows * rowlen; idx += nth) {
-            const int row = idx / rowlen, e = idx - (idx / rowlen) * rowlen;
-            const int ly = row % L1, lz = row / L1;
-            const long long g = fbase + (((long long)(org[2] + lz) * S.n[1] + (org[1] + ly)) * S.n[0] + org[0]) * NN + e;
-            f[g] = T(2) * tile[idx] - f[g];
-        }
-    }
+// One sweep over every population: blockIdx.x / bpv + k0 is the velocity.
+// MAXT bounds the block size (the subdomain's columns), which bounds
+// registers.
+template <int D, int P, typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) sx_wave_kernel(const __grid_constant__ SxWave<D, P, T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);
+    const int k = A.k0 + (int)blockIdx.x / A.bpv, lb = (int)blockIdx.x % A.bpv;
+    T* ring = xs + 4 * SxRing<D, P, T>::TNP * blockDim.x;
+    if (k == 0) sx_sweep_velocity<D, P, 0, T>(A, lb, xs, ring);
+    else if (k == 1) sx_sweep_velocity<D, P, 1, T>(A, lb, xs, ring);
+    else if (k == 2) sx_sweep_velocity<D, P, 2, T>(A, lb, xs, ring);
+    else if (D == 3) sx_sweep_velocity<D, P, 3, T>(A, lb, xs, ring);
 }
 
 // Relaxation with the d + 1 velocity equilibria: M_{k,v} = sum_j Minv[k][j] rhs_j,
@@ -585,31 +874,160 @@ static int sx_grid(long long n)
     return (int)(g < 1 ? 1 : g);
 }
 
-template <typename T>
-static cudaError_t sweep_dispatch(const SxArgs& a, cudaStream_t st, size_t smem, int grid)
+constexpr int kSxNarrow = 256;     // block sizes up to this use the register-rich instance
+
+template <int D, int P, typename T>
+static const void* wave_fn(int nt)
 {
-    const void* fn = nullptr;
-    if (a.dim == 2) {
-        if (a.degree == 1) fn = (const void*)sx_sweep_kernel<2, 1, T>;
-        if (a.degree == 2) fn = (const void*)sx_sweep_kernel<2, 2, T>;
-        if (a.degree == 3) fn = (const void*)sx_sweep_kernel<2, 3, T>;
-    } else if (a.dim == 3) {
-        if (a.degree == 1) fn = (const void*)sx_sweep_kernel<3, 1, T>;
-        if (a.degree == 2) fn = (const void*)sx_sweep_kernel<3, 2, T>;
-    }
-    if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = cudaSuccess;
-    if (smem > 48 * 1024) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    SxArgs args = a;
-    void* p[] = {&args};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kSxThreads), p, smem, st);
+    return nt <= kSxNarrow ? (const void*)sx_wave_kernel<D, P, T, kSxNarrow> : (const void*)sx_wave_kernel<D, P, T, 1024>;
 }
 
-cudaError_t sx_launch_sweep(const SxArgs& a, int prec, size_t smem, cudaStream_t st)
+template <typename T>
+static const void* wave_pick(int dim, int degree, int nt)
 {
-    const int grid = a.npop * a.NS[0] * a.NS[1] * a.NS[2];
-    return prec == 1 ? sweep_dispatch<float>(a, st, smem, grid) : sweep_dispatch<double>(a, st, smem, grid);
+    if (dim == 2) {
+        if (degree == 1) return wave_fn<2, 1, T>(nt);
+        if (degree == 2) return wave_fn<2, 2, T>(nt);
+        if (degree == 3) return wave_fn<2, 3, T>(nt);
+    } else if (dim == 3) {
+        if (degree == 1) return wave_fn<3, 1, T>(nt);
+        if (degree == 2) return wave_fn<3, 2, T>(nt);
+    }
+    return nullptr;
+}
+
+static int sx_lanes(const SxArgs& a)
+{
+    if (a.dim == 2) return a.L[0] > a.L[1] ? a.L[0] : a.L[1];
+    return a.L[0] * a.L[1];
+}
+
+// boundary lanes per transverse axis, at most (the larger transverse extent
+// over the velocities' lane layouts)
+static int sx_boundary_lanes(const SxArgs& a)
+{
+    if (a.dim == 2) return 1;
+    return a.L[0] > a.L[1] ? a.L[0] : a.L[1];
+}
+
+template <int D, int P, typename T>
+static size_t wave_smem_of(int nt, int nbm)
+{
+    using RG = SxRing<D, P, T>;
+    // exchange [2 parities][2 axes][nt][TNP] + ring [kSxRing][nt][NEP]
+    // + transverse inflow [kSxRing][2 axes][nbm][TNP]
+    return (((size_t)4 * RG::TNP + (size_t)kSxRing * RG::NEP) * nt + (size_t)kSxRing * 2 * nbm * RG::TNP) * sizeof(T);
+}
+
+template <typename T>
+static size_t wave_smem(int dim, int degree, int nt, int nbm)
+{
+    if (dim == 2) {
+        if (degree == 1) return wave_smem_of<2, 1, T>(nt, nbm);
+        if (degree == 2) return wave_smem_of<2, 2, T>(nt, nbm);
+        if (degree == 3) return wave_smem_of<2, 3, T>(nt, nbm);
+    } else if (dim == 3) {
+        if (degree == 1) return wave_smem_of<3, 1, T>(nt, nbm);
+        if (degree == 2) return wave_smem_of<3, 2, T>(nt, nbm);
+    }
+    return 0;
+}
+
+int sx_sweep_shape(const SxArgs& a, int prec, SxPlan* plan)
+{
+    const int nt = (sx_lanes(a) + 31) / 32 * 32;
+    const void* fn = prec == 1 ? wave_pick<float>(a.dim, a.degree, nt) : wave_pick<double>(a.dim, a.degree, nt);
+    const int nbm = sx_boundary_lanes(a);
+    const size_t sm = prec == 1 ? wave_smem<float>(a.dim, a.degree, nt, nbm) : wave_smem<double>(a.dim, a.degree, nt, nbm);
+    if (!fn || nt > 1024 || sm > 227 * 1024) return 0;
+    plan->threads = nt;
+    plan->smem = sm;
+    return 1;
+}
+
+cudaError_t sx_sweep_plan(const SxArgs& a, int prec, SxPlan* plan)
+{
+    if (!sx_sweep_shape(a, prec, plan)) return cudaErrorInvalidValue;
+    const void* fn = prec == 1 ? wave_pick<float>(a.dim, a.degree, plan->threads)
+                               : wave_pick<double>(a.dim, a.degree, plan->threads);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan->smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0, dev = 0, nsm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, plan->threads, plan->smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    // one resident wave of blocks, each streaming ceil(problems / blocks)
+    // problems.  When one velocity's problems alone fill that wave, the
+    // velocities go in separate launches (an SM then runs one velocity's
+    // code at a time); otherwise one launch takes them all.
+    const int nprob = a.m * a.NS[0] * a.NS[1] * a.NS[2];
+    const int slots = occ * nsm;
+    plan->split = nprob >= slots;
+    int b = plan->split ? slots : slots / a.nvel;
+    if (b < 1) b = 1;
+    if (b > nprob) b = nprob;
+    const int per = (nprob + b - 1) / b;
+    plan->bpv = (nprob + per - 1) / per;
+    plan->occupancy = occ;
+    return cudaSuccess;
+}
+
+template <int D, int P, typename T>
+static cudaError_t wave_launch(const SxArgs& a, const double* hrec, int rstride, const SxPlan& plan,
+                               cudaStream_t st)
+{
+    using WA = SxWave<D, P, T>;
+    static_assert(sizeof(WA) <= 32000, "sweep parameters exceed the kernel parameter limit");
+    constexpr int NN = WA::NN, TN = WA::TN, NV = WA::NV;
+    WA w;
+    memset(&w, 0, sizeof w);
+    w.S = a;
+    w.bpv = plan.bpv;
+    w.k0 = 0;
+    w.div_nsub = sx_div_make(a.NS[0] * a.NS[1] * a.NS[2]);
+    w.div_ns0 = sx_div_make(a.NS[0]);
+    w.div_ns1 = sx_div_make(a.NS[1]);
+    for (int k = 0; k < NV; ++k) {
+        const double* rec = hrec + (size_t)k * rstride;
+        for (int e = 0; e < NN * NN; ++e) w.ainv[k][e] = (T)rec[e];
+        for (int ax = 0; ax < D; ++ax)
+            for (int t = 0; t < TN; ++t) w.face[k][ax][t] = (T)rec[NN * NN + NN + ax * TN + t];
+    }
+    for (int j = 0; j < NN; ++j) w.wcell[j] = (T)hrec[NN * NN + j];
+    const void* fn = wave_fn<D, P, T>(plan.threads);
+    void* p[] = {&w};
+    if (!plan.split)
+        return cudaLaunchKernel(fn, dim3(a.nvel * plan.bpv), dim3(plan.threads), p, plan.smem, st);
+    for (int k = 0; k < a.nvel; ++k) {
+        w.k0 = k;
+        const cudaError_t e = cudaLaunchKernel(fn, dim3(plan.bpv), dim3(plan.threads), p, plan.smem, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t wave_dispatch(const SxArgs& a, const double* hrec, int rstride, const SxPlan& plan,
+                                 cudaStream_t st)
+{
+    if (a.dim == 2) {
+        if (a.degree == 1) return wave_launch<2, 1, T>(a, hrec, rstride, plan, st);
+        if (a.degree == 2) return wave_launch<2, 2, T>(a, hrec, rstride, plan, st);
+        if (a.degree == 3) return wave_launch<2, 3, T>(a, hrec, rstride, plan, st);
+    } else if (a.dim == 3) {
+        if (a.degree == 1) return wave_launch<3, 1, T>(a, hrec, rstride, plan, st);
+        if (a.degree == 2) return wave_launch<3, 2, T>(a, hrec, rstride, plan, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t sx_launch_sweep(const SxArgs& a, int prec, const double* hrec, int rstride, const SxPlan& plan,
+                            cudaStream_t st)
+{
+    return prec == 1 ? wave_dispatch<float>(a, hrec, rstride, plan, st)
+                     : wave_dispatch<double>(a, hrec, rstride, plan, st);
 }
 
 cudaError_t sx_launch_trace0(const SxArgs& a, int prec, cudaStream_t st)

@@ -138,7 +138,19 @@ __device__ __forceinline__ void cp16_g2s(void* sdst, const void* gsrc)
                  "l"(gsrc)
                  : "memory");
 }
+// 4- or 8-byte variant (through L1), for sources aligned to their size only
+template <int BYTES>
+__device__ __forceinline__ void cp_small_g2s(void* sdst, const void* gsrc)
+{
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async.ca takes 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((unsigned)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc), "n"(BYTES)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// all but the N most recent commit groups of this thread have landed
+template <int N>
+__device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // all but the most recent commit group of this thread have landed
 __device__ __forceinline__ void cp_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }

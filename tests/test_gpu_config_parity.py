@@ -144,3 +144,23 @@ def test_served_request_500_steps(kin):
     _, _, fe = errors(w, W, Wo, f, fo)
     print(f"[config-parity] served vortex 256^2 p3 x 500: f_max={fe:.3e}")
     assert fe < FTOL32, fe
+
+
+def test_vortex_2d_d2q3_full_size_50_steps(kin):
+    # the 2D configuration with the paper's D2Q3 velocities (Sec. 2.4) at its
+    # full size: 256^2 cells, p = 2, 8 x 8 subdomains, FP32, 50 steps.  At
+    # omega = 2 and this time step the D2Q3 scheme itself is not stable: the
+    # FP64 oracle's density leaves [0.78, 1.0001] near step 100 and overflows
+    # soon after, so the run stops well before.
+    w = workloads.vortex2d(seed=0, velset=1)
+    W, f = gpu_run(kin, w, 50)
+    _check("vortex2d D2Q3 256^2 x 50", w, W, f, 50)
+
+
+def test_density_wave_3d_d3q4_full_size_2_steps(kin):
+    # the 3D configuration with the paper's D3Q4 velocities (Sec. 6.1.3) at
+    # its full size: 128^3 cells, 16^3 subdomains (every sweep block streams
+    # many subdomains), FP32
+    w = workloads.densitywave3d(seed=0, velset=1)
+    W, f = gpu_run(kin, w, 2)
+    _check("densitywave3d D3Q4 128^3 x 2", w, W, f, 2)

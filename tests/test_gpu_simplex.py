@@ -57,10 +57,53 @@ def test_simplex_sets_match_oracle(kin, case, prec):
     np.testing.assert_allclose(mass, mo, rtol=tol * 10, atol=tol * 10)
 
 
+# Launch shapes of the streaming sweep: many (variable, subdomain) problems
+# per thread block (more problems than one resident wave of blocks), columns
+# spread over several warps (the transverse exchange crosses warps), column
+# counts that are not a multiple of 32, a 2D subdomain wider than it is high.
+STREAM_CASES = [
+    lambda prec: workloads.with_(workloads.densitywave3d(seed=6, n=16, degree=1, tiles=8, dt_mult=20.0,
+                                                         velset=1, precision=prec), tiles=(8, 8, 8)),
+    lambda prec: workloads.with_(workloads.densitywave3d(seed=7, n=16, degree=1, tiles=2, dt_mult=20.0,
+                                                         velset=1, precision=prec), tiles=(2, 2, 2)),
+    lambda prec: workloads.with_(workloads.densitywave3d(seed=8, n=24, degree=1, tiles=2, dt_mult=15.0,
+                                                         velset=1, precision=prec), tiles=(2, 3, 4)),
+    lambda prec: workloads.with_(workloads.densitywave2d(seed=9, n=128, degree=2, tiles=32, dt_mult=20.0,
+                                                         velset=1, precision=prec), tiles=(32, 32)),
+    lambda prec: workloads.with_(workloads.densitywave2d(seed=10, n=64, degree=2, tiles=1, dt_mult=20.0,
+                                                         velset=1, precision=prec), tiles=(1, 2)),
+    lambda prec: workloads.with_(workloads.densitywave2d(seed=11, n=48, degree=3, tiles=1, dt_mult=10.0,
+                                                         velset=1, precision=prec), tiles=(3, 1), iters=2),
+]
+
+
+@pytest.mark.parametrize("case", range(len(STREAM_CASES)))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_simplex_stream_shapes_match_oracle(kin, case, prec):
+    w = STREAM_CASES[case](prec)
+    steps = 3
+    with kin.Context.from_workload(w) as ctx:
+        ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+        ctx.step(steps)
+        W = ctx.get_state()
+        f = ctx.get_kinetic()
+    P = oracle.Problem(**w.oracle_kwargs())
+    fo = oracle.init(P, w.W0)
+    oracle.step(P, fo, steps)
+    Wo = oracle.moments(P, fo)
+    l2, linf = rel_errors(w, W, Wo)
+    tol = TOL64 if prec == "f64" else TOL32
+    assert l2 < tol and linf < tol, (l2, linf)
+    f = f.reshape(w.npop, -1)
+    fo = fo.reshape(w.npop, -1)
+    fe = max(np.abs(f[k] - fo[k]).max() / np.abs(fo[k]).max() for k in range(w.npop))
+    assert fe < (TOL64 if prec == "f64" else 5 * TOL32), fe
+
+
 def test_simplex_errors(kin):
-    w = workloads.densitywave2d(seed=1, n=256, degree=3, tiles=1, velset=1)
+    w = workloads.densitywave3d(seed=1, n=64, degree=1, tiles=1, velset=1)
     with pytest.raises(kin.KinError) as ei:
-        kin.Context.from_workload(w)          # one subdomain of 256^2 cells does not fit
+        kin.Context.from_workload(w)          # 64 x 64 columns per subdomain: more than 1024 lanes
     assert ei.value.status == kin.KIN_EINVAL
     w = workloads.with_(workloads.densitywave2d(seed=1, n=16, degree=1, tiles=2, velset=1), tiles=(2, 2))
     with kin.Context.from_workload(w) as ctx:
