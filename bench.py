@@ -87,12 +87,12 @@ def flops_per_dof(dim, degree, m, nvel, maxwell=False):
 # launches), scaled from a capture of a smaller mix by the kinetic DOF.
 NCU_TRAFFIC = {
     # 64-instance batched mix, one step = three launches (degree 2, 1, 3):
-    # read 674.2 + 497.6 + 3411 MB, write 619.9 + 439.8 + 3361 MB
-    ("batched", "f32"): (9.0035e9, "eed7a2e564c5b11d"),
+    # read 674.4 + 497.6 + 3411.7 MB, write 619.8 + 439.9 + 3361.0 MB
+    ("batched", "f32"): (9.0044e9, "92f2ff9b2905ce7d"),
 }
 # the same capture per launch, keyed by degree
-NCU_TRAFFIC_PER_DEGREE = {1: (0.9374e9, "eed7a2e564c5b11d"), 2: (1.2941e9, "eed7a2e564c5b11d"),
-                          3: (6.772e9, "eed7a2e564c5b11d")}
+NCU_TRAFFIC_PER_DEGREE = {1: (0.9375e9, "92f2ff9b2905ce7d"), 2: (1.2942e9, "92f2ff9b2905ce7d"),
+                          3: (6.7727e9, "92f2ff9b2905ce7d")}
 
 
 # device sources of the axis-velocity step kernels (single, batched, mixed)

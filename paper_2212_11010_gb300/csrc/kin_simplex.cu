@@ -752,7 +752,7 @@ __device__ __forceinline__ void sx_sweep_velocity(const SxWave<D, P, T>& A, cons
 template <int D, int P, typename T, int MAXT>
 __global__ void __launch_bounds__(MAXT) sx_wave_kernel(const __grid_constant__ SxWave<D, P, T> A)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);
     const int k = A.k0 + (int)blockIdx.x / A.bpv, lb = (int)blockIdx.x % A.bpv;
     T* ring = xs + 4 * SxRing<D, P, T>::TNP * blockDim.x;
