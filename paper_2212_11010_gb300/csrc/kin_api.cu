@@ -77,8 +77,7 @@ struct kin_ctx {
     int* torder = nullptr;            // [velocity][cells]
     int* tlstart = nullptr;           // [velocity][nsub + 1]
     int* tbounds = nullptr;           // level boundaries
-    int* tfnodes = nullptr;           // [cell][4][3]
-    int* tiface = nullptr;            // [cell]
+    int* tfref = nullptr;             // [velocity][position][4][3] inflow face vertex references
     void* titer[2] = {nullptr, nullptr};   // subdomain iterates
     std::vector<double> tvol;         // host: cell volumes, for the mass diagnostic
     bool have_state = false;
@@ -499,8 +498,7 @@ static TetArgs tet_args(const kin_ctx* c)
     a.order = c->torder;
     a.lstart = c->tlstart;
     a.bounds = c->tbounds;
-    a.fnodes = c->tfnodes;
-    a.iface = c->tiface;
+    a.fref = c->tfref;
     a.f = c->f;
     a.lambda = c->lambda;
     a.gamma = c->gamma;
@@ -1021,6 +1019,19 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
             bounds.push_back(pos);
         }
     }
+    // inflow face vertices per (velocity, position in its order): the
+    // neighbour's node, doubled, + 1 when the face is a subdomain interface
+    std::vector<int> fref((size_t)c->nvel * n * 12, 0);
+    for (int k = 0; k < c->nvel; ++k)
+        for (int q = 0; q < n; ++q) {
+            const int cc = order[(size_t)k * n + q];
+            for (int a = 0; a < 4; ++a) {
+                if (((ftype[(size_t)k * n + cc] >> (2 * a)) & 3) != 1) continue;
+                for (int jj = 0; jj < 3; ++jj)
+                    fref[((size_t)k * n + q) * 12 + a * 3 + jj] =
+                        2 * fnodes[(size_t)cc * 12 + a * 3 + jj] + ((iface[cc] >> a) & 1);
+            }
+        }
 
     kin_status st;
     void* p;
@@ -1041,8 +1052,7 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
     ALLOC(c->torder, sizeof(int) * order.size());
     ALLOC(c->tlstart, sizeof(int) * lstart.size());
     ALLOC(c->tbounds, sizeof(int) * bounds.size());
-    ALLOC(c->tfnodes, sizeof(int) * fnodes.size());
-    ALLOC(c->tiface, sizeof(int) * iface.size());
+    ALLOC(c->tfref, sizeof(int) * fref.size());
     ALLOC(c->Wbuf, sizeof(double) * c->m * c->nodes);
     ALLOC(c->errword, sizeof(int) * 4);
     // FP64 setup scratch: vertex coordinates, face types, FP64 records
@@ -1064,9 +1074,7 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->tbounds, bounds.data(), sizeof(int) * bounds.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->tfnodes, fnodes.data(), sizeof(int) * fnodes.size(), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->tiface, iface.data(), sizeof(int) * iface.size(), cudaMemcpyHostToDevice, c->stream);
+        e = cudaMemcpyAsync(c->tfref, fref.data(), sizeof(int) * fref.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(xyz_d, mesh->xyz, sizeof(double) * 12 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ft_d, ftype.data(), ftype.size(), cudaMemcpyHostToDevice, c->stream);

@@ -112,8 +112,7 @@ struct TetArgs {
     const int* order;             // [velocity][ncells]: cells by subdomain, then breadth-first
     const int* lstart;            // [velocity][nsub + 1]: first level index of each subdomain in bounds
     const int* bounds;            // level l of the order holds positions [bounds[l], bounds[l + 1])
-    const int* fnodes;            // [cell][face a][3]: the neighbour's node (R * 4 + j) at each vertex of the face
-    const int* iface;             // [cell]: bit a set when face a is a subdomain interface
+    const int* fref;              // [velocity][position][face a][3]: 2 (neighbour's node) + 1 at an interface
     void* f;                      // T [pop][cell][4]
     double lambda, gamma, omega, mu;
     double adv[3];

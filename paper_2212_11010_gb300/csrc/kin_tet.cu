@@ -169,69 +169,109 @@ __device__ __forceinline__ void store4(T* p, const T (&u)[4])
 
 // Every thread takes one (cell, variable) pair of the level: the m threads
 // of a cell read the same coefficient record (one broadcast), and a level of
-// c cells offers c m independent solves.
+// c cells offers c m independent solves.  The inflow face vertices are
+// resolved ahead of time, per position of the velocity's level order:
+// fref = 2 (global node) + 1 when the face is a subdomain interface (the
+// value comes from the previous iterate), + 0 otherwise (the current one).
+// A thread's first pair of a level has its cell loaded two levels ahead and
+// its face references and f^n one level ahead, so a level waits for one
+// round of loads (its cells' records and neighbour values, issued together)
+// rather than for a chain of dependent ones.
 template <typename T>
 __global__ void __launch_bounds__(kTetSweepThreads) tet_sweep_kernel(TetArgs A, const T* __restrict__ prev, T* cur)
 {
     const int s = blockIdx.x, k = blockIdx.y;
     const int* __restrict__ order = A.order + (size_t)k * A.ncells;
+    const int* __restrict__ fref = A.fref + (size_t)k * A.ncells * 12;
     const int lb = A.lstart[k * (A.nsub + 1) + s], le = A.lstart[k * (A.nsub + 1) + s + 1];
     const T* __restrict__ coef = static_cast<const T*>(A.coef) + (size_t)k * A.ncells * kTetRec;
     const T* __restrict__ fn = static_cast<const T*>(A.f);
     const long long nodes = A.nodes;
     const int m = A.m;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    auto solve = [&](int pos, int v, int c, const int (&nr)[12]) {
+        const T* rec = coef + (size_t)pos * kTetRec;
+        const long long pop = (long long)(k * m + v) * nodes;
+        T u[4];
+        load4(fn + pop + (size_t)c * 4, u);
+        const T r = u[0];
+        T du[4], sum = T(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            du[i] = u[i] - r;
+            sum += du[i];
+        }
+        const T m20 = rec[16];
+        T rhs[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rhs[i] = m20 * (sum + du[i]);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const T ca = rec[17 + a];
+            if (ca == T(0)) continue;
+            // the neighbour's values at this cell's face vertices (j != a, ascending)
+            T g[4] = {T(0), T(0), T(0), T(0)};
+            T gs = T(0);
+            int jj = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j == a) continue;
+                const int ref = nr[a * 3 + jj];
+                g[j] = ((ref & 1) ? prev : cur)[pop + (ref >> 1)] - r;
+                gs += g[j];
+                ++jj;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i != a) rhs[i] = fma(ca, gs + g[i], rhs[i]);
+        }
+        T x[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            T acc = rec[i * 4] * rhs[0];
+#pragma unroll
+            for (int j = 1; j < 4; ++j) acc = fma(rec[i * 4 + j], rhs[j], acc);
+            x[i] = acc + r;
+        }
+        store4(cur + pop + (size_t)c * 4, x);
+    };
+    auto refs = [&](int pos, int (&nr)[12]) {
+        const int4* q = reinterpret_cast<const int4*>(fref + (size_t)pos * 12);
+#pragma unroll
+        for (int w = 0; w < 3; ++w) {
+            const int4 e = q[w];
+            nr[4 * w] = e.x;
+            nr[4 * w + 1] = e.y;
+            nr[4 * w + 2] = e.z;
+            nr[4 * w + 3] = e.w;
+        }
+    };
+
+    // this thread's first pair of the coming level: cell and face references
+    int cn = 0, nrn[12];
+    if (lb < le && tid < (A.bounds[lb + 1] - A.bounds[lb]) * m) {
+        const int pos = A.bounds[lb] + tid / m;
+        cn = order[pos];
+        refs(pos, nrn);
+    }
     for (int l = lb; l < le; ++l) {
         const int p0 = A.bounds[l], p1 = A.bounds[l + 1];
         const int items = (p1 - p0) * m;
-        for (int it = threadIdx.x; it < items; it += blockDim.x) {
-            const int q = it / m, v = it - q * m;
-            const int c = order[p0 + q];
-            const T* rec = coef + (size_t)(p0 + q) * kTetRec;
-            const long long pop = (long long)(k * m + v) * nodes;
-            T u[4];
-            load4(fn + pop + (size_t)c * 4, u);
-            const T r = u[0];
-            T du[4], sum = T(0);
+        int cc = cn, nrc[12];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                du[i] = u[i] - r;
-                sum += du[i];
-            }
-            const T m20 = rec[16];
-            T rhs[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) rhs[i] = m20 * (sum + du[i]);
-            const int* fnode = A.fnodes + (size_t)c * 12;
-            const int iface = A.iface[c];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const T ca = rec[17 + a];
-                if (ca == T(0)) continue;
-                const T* src = ((iface >> a) & 1) ? prev : cur;
-                // the neighbour's values at this cell's face vertices (j != a, ascending)
-                T g[4] = {T(0), T(0), T(0), T(0)};
-                T gs = T(0);
-                int jj = 0;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (j == a) continue;
-                    g[j] = src[pop + fnode[a * 3 + jj]] - r;
-                    gs += g[j];
-                    ++jj;
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (i != a) rhs[i] = fma(ca, gs + g[i], rhs[i]);
-            }
-            T x[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                T acc = rec[i * 4] * rhs[0];
-#pragma unroll
-                for (int j = 1; j < 4; ++j) acc = fma(rec[i * 4 + j], rhs[j], acc);
-                x[i] = acc + r;
-            }
-            store4(cur + pop + (size_t)c * 4, x);
+        for (int i = 0; i < 12; ++i) nrc[i] = nrn[i];
+        if (l + 1 < le && tid < (A.bounds[l + 2] - p1) * m) {
+            const int pos = p1 + tid / m;
+            cn = order[pos];
+            refs(pos, nrn);
+        }
+        if (tid < items) solve(p0 + tid / m, tid % m, cc, nrc);
+        for (int it = tid + nt; it < items; it += nt) {
+            const int pos = p0 + it / m;
+            int nr[12];
+            refs(pos, nr);
+            solve(pos, it % m, order[pos], nr);
         }
         __syncthreads();     // the next level reads this level's cells
     }
