@@ -736,10 +736,13 @@ __device__ __forceinline__ void sx_sweep_velocity(const SxWave<D, P, T>& A, cons
         fetch(tp, k);
     }
     for (int W = 0; W < total; ++W) {
+        // with one wave in flight the prefetch position of the last wave is
+        // this wave's: copy it rather than advance a second tracker
+        if constexpr (PF == 1) tc = tp;
         advance(tp);
         fetch(tp, (W + PF) % kSxRing);             // wave W + PF
         cp_wait_group<PF>();                        // wave W has landed
-        advance(tc);
+        if constexpr (PF != 1) advance(tc);
         compute(W, tc, W % kSxRing);
         __syncthreads();
     }
