@@ -245,6 +245,24 @@ kin_status kin_get_state(kin_ctx* ctx, double* W, size_t n_values, int on_device
 /* Copy out the kinetic state f (npop * nodes values of the context precision). */
 kin_status kin_get_kinetic(kin_ctx* ctx, void* f, size_t n_values, int on_device);
 
+/* Host copies for pipelines.  As kin_set_kinetic and kin_get_kinetic with a
+ * host buffer, but enqueued on `stream` (a cudaStream_t; NULL = the context's
+ * stream) and not waited for.  After kin_set_kinetic_async the interface
+ * summaries of the new f (axis velocity sets) are computed by the next
+ * kin_step, kin_batch_step or defect diagnostic: a batch does it for all its
+ * members in one pass per kernel type.
+ * Ownership: f stays the caller's.  It must be page-locked host memory and
+ * must not be modified (set) or read (get) until the copy has completed; the
+ * caller orders that with an event or a stream synchronisation.
+ * Ordering: the caller orders these copies against kin_step or
+ * kin_batch_step on other streams with events (cudaStreamWaitEvent).  A copy
+ * and a step of the same context must not overlap in time.
+ * Errors: KIN_EINVAL (NULL f, wrong n_values) and KIN_ESTATE (get before any
+ * state) at the call.  A failure of the enqueued work shows at the next
+ * synchronising call (kin_sync, kin_get_state, kin_diag). */
+kin_status kin_set_kinetic_async(kin_ctx* ctx, const void* f, size_t n_values, void* stream);
+kin_status kin_get_kinetic_async(kin_ctx* ctx, void* f, size_t n_values, void* stream);
+
 /* FP64 diagnostics, synchronous.  mass_per_var (m doubles, may be NULL): the
  * quadrature integral of every conserved variable over the box.
  * next_defect (m doubles, may be NULL): the mass change that the next step's

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "KIN_OK", 1: "KIN_EINVAL", 2: "KIN_ENOMEM", 3: "KIN_EBUDGET",
                 4: "KIN_ECUDA", 5: "KIN_ETIMEOUT", 6: "KIN_ESTATE"}
 
 EXPORTED = ["kin_create", "kin_set_state", "kin_set_kinetic", "kin_step", "kin_get_state",
-            "kin_get_kinetic", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error",
+            "kin_get_kinetic", "kin_set_kinetic_async", "kin_get_kinetic_async", "kin_diag", "kin_sync", "kin_query", "kin_destroy", "kin_last_error",
             "kin_step_noalloc", "kin_batch_create", "kin_batch_create_ex", "kin_batch_step", "kin_batch_sync",
             "kin_batch_destroy", "kin_batch_last_error", "kin_set_boundary", "kin_batch_info", "kin_create_tet"]
 
@@ -107,6 +107,8 @@ def load_library():
     lib.kin_step.argtypes = [vp, ctypes.c_int]
     lib.kin_get_state.argtypes = [vp, vp, sz, ctypes.c_int]
     lib.kin_get_kinetic.argtypes = [vp, vp, sz, ctypes.c_int]
+    lib.kin_set_kinetic_async.argtypes = [vp, vp, sz, vp]
+    lib.kin_get_kinetic_async.argtypes = [vp, vp, sz, vp]
     lib.kin_diag.argtypes = [vp, dp, dp, dp]
     lib.kin_sync.argtypes = [vp]
     lib.kin_query.argtypes = [vp, ctypes.POINTER(kin_info)]
@@ -207,6 +209,24 @@ def kin_set_kinetic(ctx, f, n_values=None):
     p, dev = _ptr(f)
     n = f.size if isinstance(f, np.ndarray) else f.numel()
     _check(ctx, load_library().kin_set_kinetic(ctx, p, n if n_values is None else n_values, dev))
+
+
+def _host_ptr(a):
+    """Address and size of a page-locked host torch tensor (the async copies
+    need one; a pageable numpy array would make the copy synchronous)."""
+    if not (hasattr(a, "is_pinned") and a.is_pinned()):
+        raise ValueError("the asynchronous host copies take a page-locked torch tensor")
+    return ctypes.c_void_p(a.data_ptr()), a.numel()
+
+
+def kin_set_kinetic_async(ctx, f, stream=None):
+    p, n = _host_ptr(f)
+    _check(ctx, load_library().kin_set_kinetic_async(ctx, p, n, stream))
+
+
+def kin_get_kinetic_async(ctx, f, stream=None):
+    p, n = _host_ptr(f)
+    _check(ctx, load_library().kin_get_kinetic_async(ctx, p, n, stream))
 
 
 def kin_step(ctx, nsteps: int):

@@ -81,6 +81,7 @@ struct kin_ctx {
     void* titer[2] = {nullptr, nullptr};   // subdomain iterates
     std::vector<double> tvol;         // host: cell volumes, for the mass diagnostic
     bool have_state = false;
+    bool sum_stale = false;           // f was replaced without recomputing the interface summaries
     long long steps_done = 0;
     bool poisoned = false;
     std::string err;
@@ -381,7 +382,7 @@ static cudaError_t configure_launch(kin_ctx* c)
 // mode 1 = block summaries of the current state only, written straight into
 // buffer cur (mode 1 reads no summaries), so cur stays: a state set through
 // kin_set_state / kin_set_kinetic keeps a member's batch valid.
-static kin_status launch_step(kin_ctx* c, int mode)
+static kin_status launch_step_on(kin_ctx* c, int mode, cudaStream_t st)
 {
     Inst I = make_inst(c, mode);
     if (mode == 1) {
@@ -390,10 +391,12 @@ static kin_status launch_step(kin_ctx* c, int mode)
     }
     void* args[] = {&I};
     KIN_CUDA(c, cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(c->threads), args,
-                                 (size_t)c->smem, c->stream));
+                                 (size_t)c->smem, st));
     if (mode == 0) c->cur ^= 1;
     return KIN_OK;
 }
+
+static kin_status launch_step(kin_ctx* c, int mode) { return launch_step_on(c, mode, c->stream); }
 
 static PointArgs point_args(const kin_ctx* c)
 {
@@ -1143,6 +1146,7 @@ kin_status kin_set_state(kin_ctx* c, const double* W, size_t n_values, int on_de
         st = launch_step(c, 1);
         if (st) return st;
     }
+    c->sum_stale = false;
     c->have_state = true;
     c->steps_done = 0;
     if (!on_device) {
@@ -1165,11 +1169,41 @@ kin_status kin_set_kinetic(kin_ctx* c, const void* f, size_t n_values, int on_de
         st = launch_step(c, 1);
         if (st) return st;
     }
+    c->sum_stale = false;
     c->have_state = true;
     if (!on_device) {
         KIN_CUDA(c, cudaStreamSynchronize(c->stream));
         return check_errword(c);
     }
+    return KIN_OK;
+}
+
+kin_status kin_set_kinetic_async(kin_ctx* c, const void* f, size_t n_values, void* stream)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (!f) return fail(c, KIN_EINVAL, "f is NULL");
+    if (n_values != (size_t)c->npop * c->nodes)
+        return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    KIN_CUDA(c, cudaMemcpyAsync(c->f, f, n_values * c->esize, cudaMemcpyHostToDevice, s));
+    // the interface summaries of the new f are computed by the next step
+    // (kin_step, kin_batch_step) or diagnostic that needs them
+    if (!c->simplex && !c->tet) c->sum_stale = true;
+    c->have_state = true;
+    return KIN_OK;
+}
+
+kin_status kin_get_kinetic_async(kin_ctx* c, void* f, size_t n_values, void* stream)
+{
+    kin_status st = check_usable(c);
+    if (st) return st;
+    if (!f) return fail(c, KIN_EINVAL, "f is NULL");
+    if (n_values != (size_t)c->npop * c->nodes)
+        return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
+    if (!c->have_state) return fail(c, KIN_ESTATE, "no state has been set");
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    KIN_CUDA(c, cudaMemcpyAsync(f, c->f, n_values * c->esize, cudaMemcpyDeviceToHost, s));
     return KIN_OK;
 }
 
@@ -1222,6 +1256,11 @@ kin_status kin_step(kin_ctx* c, int nsteps)
     if (!c->have_state) return fail(c, KIN_ESTATE, "no state: call kin_set_state or kin_set_kinetic first");
     if (const char* face = missing_boundary(c))
         return fail(c, KIN_ESTATE, "the %s face of an inflow axis has no boundary state (kin_set_boundary)", face);
+    if (nsteps > 0 && c->sum_stale) {
+        st = launch_step(c, 1);
+        if (st) return st;
+        c->sum_stale = false;
+    }
     for (int s = 0; s < nsteps; ++s) {
         st = c->tet ? tet_step(c) : (c->simplex ? sx_step(c) : launch_step(c, 0));
         if (st) return st;
@@ -1308,6 +1347,11 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
             for (int v = 0; v < c->m; ++v) next_defect[v] = NAN;
         if (iter_residual) *iter_residual = NAN;
     } else if (next_defect || iter_residual) {
+        if (c->sum_stale) {
+            st = launch_step(c, 1);
+            if (st) return st;
+            c->sum_stale = false;
+        }
         DefectArgs da;
         memset(&da, 0, sizeof da);
         da.dim = c->dim;
@@ -1408,6 +1452,7 @@ struct kin_batch {
         std::vector<int> members;     // indices into kin_batch::members
         int nwork = 0;
         Inst* insts[2] = {nullptr, nullptr};   // launch records for summary parity 0 / 1
+        Inst* prep[2] = {nullptr, nullptr};    // summaries-only records (members whose f was replaced)
         int2* work = nullptr;
     };
     std::vector<kin_ctx*> members;
@@ -1459,11 +1504,11 @@ static void batch_release(kin_batch* b)
 
 // Enqueue launch k of a batch step (a kernel-type group, then the solo
 // members) at summary parity q (members' cur = expect_cur ^ q) on stream st.
-static cudaError_t batch_launch(kin_batch* b, size_t k, int q, cudaStream_t st)
+static cudaError_t batch_launch(kin_batch* b, size_t k, int q, cudaStream_t st, bool prep = false)
 {
     if (k < b->groups.size()) {
         auto& g = b->groups[k];
-        const Inst* insts = g.insts[q];
+        const Inst* insts = prep ? g.prep[q] : g.insts[q];
         const int2* work = g.work;
         int nwork = g.nwork;
         void* args[] = {(void*)&insts, (void*)&work, (void*)&nwork};
@@ -1473,7 +1518,11 @@ static cudaError_t batch_launch(kin_batch* b, size_t k, int q, cudaStream_t st)
     kin_ctx* c = b->members[mi];
     const int saved = c->cur;
     c->cur = b->expect_cur[mi] ^ q;
-    Inst I = make_inst(c, 0);
+    Inst I = make_inst(c, prep ? 1 : 0);
+    if (prep) {
+        I.sig_out = c->sig[c->cur];
+        I.raw_out = c->raw[c->cur];
+    }
     c->cur = saved;
     void* args[] = {&I};
     return cudaLaunchKernel((const void*)c->kfn, dim3(c->grid), dim3(c->threads), args, (size_t)c->smem, st);
@@ -1620,7 +1669,7 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
         auto& g = b->groups[gi];
         if (e != cudaSuccess) break;
         const bool mixed = gi == 0 && b->nmixed > 0;
-        std::vector<Inst> h[2];
+        std::vector<Inst> h[2], hp[2];
         std::vector<int2> work;
         for (size_t k = 0; k < g.members.size(); ++k) {
             kin_ctx* c = b->members[g.members[k]];
@@ -1628,6 +1677,10 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
             for (int q = 0; q < 2; ++q) {
                 c->cur = b->expect_cur[g.members[k]] ^ q;
                 h[q].push_back(make_inst(c, 0));
+                Inst I = make_inst(c, 1);
+                I.sig_out = c->sig[c->cur];
+                I.raw_out = c->raw[c->cur];
+                hp[q].push_back(I);
             }
             c->cur = saved;
             const int ntiles = c->nblk[0] * c->nblk[1] * c->nblk[2];
@@ -1652,15 +1705,17 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
         int occ = 1;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g.fn, g.threads, g.smem);
         g.grid = (int)std::min<long long>(g.nwork, (long long)std::max(occ, 1) * nsm);
-        for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
-            void* p = nullptr;
-            e = cudaMalloc(&p, sizeof(Inst) * h[q].size());
-            if (e == cudaSuccess) {
-                b->dev.push_back(p);
-                g.insts[q] = (Inst*)p;
-                e = cudaMemcpy(p, h[q].data(), sizeof(Inst) * h[q].size(), cudaMemcpyHostToDevice);
+        for (int q = 0; q < 2 && e == cudaSuccess; ++q)
+            for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+                const std::vector<Inst>& src = kind == 0 ? h[q] : hp[q];
+                void* p = nullptr;
+                e = cudaMalloc(&p, sizeof(Inst) * src.size());
+                if (e == cudaSuccess) {
+                    b->dev.push_back(p);
+                    (kind == 0 ? g.insts[q] : g.prep[q]) = (Inst*)p;
+                    e = cudaMemcpy(p, src.data(), sizeof(Inst) * src.size(), cudaMemcpyHostToDevice);
+                }
             }
-        }
         if (e == cudaSuccess) {
             void* p = nullptr;
             e = cudaMalloc(&p, sizeof(int2) * work.size());
@@ -1709,6 +1764,16 @@ extern "C" kin_status kin_batch_step(kin_batch* b, int nsteps)
     for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i) {
         e = cudaEventRecord(b->ev_member[i], b->members[i]->stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_member[i], 0);
+    }
+    // members whose f was replaced by kin_set_kinetic_async: one summaries
+    // pass over every member, one launch per kernel type, before the step
+    bool stale = false;
+    for (auto* c : b->members) stale = stale || c->sum_stale;
+    if (stale) {
+        const size_t nl = b->groups.size() + b->solo.size();
+        for (size_t k = 0; k < nl && e == cudaSuccess; ++k) e = batch_launch(b, k, b->parity, b->stream, true);
+        if (e == cudaSuccess)
+            for (auto* c : b->members) c->sum_stale = false;
     }
     if (b->direct) {
         if (e == cudaSuccess) e = batch_enqueue_steps(b, b->parity, nsteps);

@@ -173,3 +173,86 @@ def test_mixed_degrees_share_one_launch(kin):
     for a, b, want in zip(res[True], res[False], alone):
         assert np.array_equal(a, want)
         assert np.array_equal(b, want)
+
+
+def test_async_host_copies_pipeline_equals_synchronous(kin):
+    # the pipelined host round trip of the e2e measurement (each member's
+    # result copied out on one stream, its next input in on another, ordered
+    # per member by an event) gives bitwise the synchronous round trip
+    import torch
+    ws, blocks = _mix()
+    ws, blocks = ws[:5], blocks[:5]
+    steps = 3
+
+    def run(pipelined):
+        ctxs = [_ctx(kin, w, b) for w, b in zip(ws, blocks)]
+        dt = lambda c: torch.float32 if c.info.precision == kin.KIN_FP32 else torch.float64
+        fh = [torch.empty(c.info.kinetic_values, dtype=dt(c), pin_memory=True) for c in ctxs]
+        for c, h in zip(ctxs, fh):
+            kin.kin_get_kinetic(c.ctx, h.numpy())
+        stream = torch.cuda.Stream()
+        with kin.Batch(ctxs, stream=stream.cuda_stream) as b:
+            if pipelined:
+                s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+                left = [torch.cuda.Event() for _ in ctxs]
+                arrived, stepped = torch.cuda.Event(), torch.cuda.Event()
+                for _ in range(steps):
+                    for c, h, ev in zip(ctxs, fh, left):
+                        s_in.wait_event(ev)
+                        kin.kin_set_kinetic_async(c.ctx, h, s_in.cuda_stream)
+                    arrived.record(s_in)
+                    stream.wait_event(arrived)
+                    b.step(1)
+                    stepped.record(stream)
+                    s_out.wait_event(stepped)
+                    for c, h, ev in zip(ctxs, fh, left):
+                        kin.kin_get_kinetic_async(c.ctx, h, s_out.cuda_stream)
+                        ev.record(s_out)
+                torch.cuda.synchronize()
+            else:
+                for _ in range(steps):
+                    for c, h in zip(ctxs, fh):
+                        kin.kin_set_kinetic(c.ctx, h.numpy())
+                    b.step(1)
+                    b.sync()
+                    for c, h in zip(ctxs, fh):
+                        kin.kin_get_kinetic(c.ctx, h.numpy())
+        out = [h.numpy().copy() for h in fh]
+        for c in ctxs:
+            c.close()
+        return out
+
+    a, p = run(False), run(True)
+    for x, y in zip(a, p):
+        assert np.array_equal(x, y)
+    with _ctx(kin, ws[0], blocks[0]) as c:
+        with pytest.raises(ValueError):
+            kin.kin_set_kinetic_async(c.ctx, np.zeros(c.info.kinetic_values, dtype=np.float32))
+        h = torch.empty(3, dtype=torch.float32, pin_memory=True)
+        with pytest.raises(kin.KinError) as ei:
+            kin.kin_get_kinetic_async(c.ctx, h)
+        assert ei.value.status == kin.KIN_EINVAL
+
+
+def test_async_set_then_step_equals_synchronous(kin):
+    # a context stepped alone after kin_set_kinetic_async computes the
+    # deferred interface summaries itself: the same state as after the
+    # synchronous kin_set_kinetic, bitwise; the defect diagnostic too
+    import torch
+    w = workloads.vortex2d(seed=11, n=64, degree=2, tiles=2, dt_mult=6.0)
+    out = []
+    for use_async in (False, True):
+        with _ctx(kin, w, None) as c:
+            c.step(2)
+            h = torch.empty(c.info.kinetic_values, dtype=torch.float32, pin_memory=True)
+            kin.kin_get_kinetic(c.ctx, h.numpy())
+            if use_async:
+                kin.kin_set_kinetic_async(c.ctx, h)
+                torch.cuda.synchronize()
+            else:
+                kin.kin_set_kinetic(c.ctx, h.numpy())
+            _, dfc, _ = c.diag()
+            c.step(3)
+            out.append((c.get_kinetic(), dfc))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
