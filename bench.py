@@ -725,19 +725,22 @@ def run_batched(args):
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     left = [torch.cuda.Event() for _ in ctxs]
     arrived, stepped = torch.cuda.Event(), torch.cuda.Event()
+    # largest instances first: the input copy that trails the last result
+    # out is then the smallest
+    order = sorted(range(len(ctxs)), key=lambda i: -ctxs[i].info.kinetic_values)
     with kin.Batch(ctxs, stream=stream.cuda_stream, mixed=sched.mixed) as b:
         def e2e_step():
-            for c, h, ev in zip(ctxs, fh, left):
-                s_in.wait_event(ev)                 # this instance's last result has left
-                kin.kin_set_kinetic_async(c.ctx, h, s_in.cuda_stream)
+            for i in order:
+                s_in.wait_event(left[i])            # this instance's last result has left
+                kin.kin_set_kinetic_async(ctxs[i].ctx, fh[i], s_in.cuda_stream)
             arrived.record(s_in)
             stream.wait_event(arrived)
             b.step(1)
             stepped.record(stream)
             s_out.wait_event(stepped)
-            for c, h, ev in zip(ctxs, fh, left):
-                kin.kin_get_kinetic_async(c.ctx, h, s_out.cuda_stream)
-                ev.record(s_out)
+            for i in order:
+                kin.kin_get_kinetic_async(ctxs[i].ctx, fh[i], s_out.cuda_stream)
+                left[i].record(s_out)
         e2e_step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
