@@ -3,15 +3,18 @@
 // inflow face on every axis with V_a != 0, the downwind order is a true
 // anti-diagonal wavefront (Sec. 3.2), and subdomains meet at corners
 // (Sec. 5.1, the three-iteration case).  The transport is done by the
-// subdomain iteration of eq. ibvp as written:
-//   trace pass   iterate 0: outflow faces of f^n on every subdomain boundary;
-//   K sweeps     one thread block per (population, subdomain) holds the
-//                subdomain in shared memory and visits its cells by wavefronts;
-//                each cell solves its full local block (eq. dg_imp, CN half
-//                step) with inflow from upwind faces inside the subdomain
-//                (shared memory) or across the interface (previous iterate's
-//                traces); the sweep writes this iterate's outflow traces and,
-//                on the last iterate, f^{n+1} = 2 f* - f^n;
+// subdomain iteration of eq. ibvp as written, K sweeps per step:
+//   sweep        one launch per iterate (per velocity when a velocity alone
+//                fills the GPU): a thread block streams (variable, subdomain)
+//                problems through the subdomain's columns, one cell per lane
+//                and wave, lanes skewed so that every upwind neighbour is done
+//                the wave before (sx_sweep_velocity); each cell solves its
+//                full local block (eq. dg_imp, CN half step) with inflow from
+//                its own previous cell, the neighbouring lane, or across the
+//                interface (f^n on iterate 1, else the previous iterate's
+//                traces); downwind boundary cells write this iterate's traces;
+//                the last iterate writes f^{n+1} = 2 f* - f^n; with K = 1 a
+//                trace pass first copies iterate 0;
 //   relaxation   W = sum_k f_k and f_k <- omega M_k(W) + (1 - omega) f_k with
 //                M from the moment system eq. maxwell_def (its inverse is
 //                precomputed in FP64).
