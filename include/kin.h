@@ -65,9 +65,11 @@ enum { KIN_ADVECTION = 0, KIN_EULER = 1, KIN_MAXWELL = 2 };
  * V_k = lambda (cos 2k pi/3, sin 2k pi/3) (Sec. 2.4) and D3Q4 with the cube
  * diagonals (+-lambda, +-lambda, +-lambda) (Sec. 6.1.3), whose Maxwellians
  * solve eq. maxwell_def exactly.  The d + 1 sets are transported by K
- * literal subdomain iterations with wavefront sweeps (one subdomain of one
- * population in shared memory, so a subdomain may hold at most 227 KB of
- * one population); kin_diag's next_defect is not available for them. */
+ * literal subdomain iterations with wavefront sweeps whose lanes are the
+ * subdomain's columns along its sweep axis: a subdomain may have at most 1024
+ * columns (2D: max(L0, L1); 3D: L0 L1), else kin_create returns KIN_EINVAL;
+ * degree <= 3 in 2D, <= 2 in 3D; periodic axes only.  kin_diag's
+ * next_defect is not available for them. */
 enum { KIN_D1Q2 = 1, KIN_D2Q4 = 2, KIN_D3Q6 = 3, KIN_D2Q3 = 4, KIN_D3Q4 = 5 };
 enum { KIN_FP64 = 0, KIN_FP32 = 1 };                /* kin_opts.precision */
 
