@@ -152,3 +152,33 @@ def test_d3q4_euler_converges():
         W = oracle.moments(P, f).reshape(w.m, -1)
         errs.append(np.abs(W - w.exact(ns * w.dt)).max())
     assert errs[1] < errs[0] / 1.5, errs
+
+
+def _two_by_two(simplex, iters, cfl=0.5):
+    # 24^2 cells, p = 1, 2 x 2 periodic subdomains of 12^2 cells; a small time
+    # step (|V| dt = cfl h) so that a subdomain's influence across its
+    # neighbour within one step is far below round-off
+    lam = 1.3
+    kw = dict(velset=oracle.SIMPLEX) if simplex else {}
+    return oracle.Problem(dim=2, n=(24, 24), lo=(0.0, 0.0), hi=(1.0, 1.0), degree=1, system=oracle.ADVECTION,
+                          lam=lam, dt=cfl / 24 / lam, tiles=(2, 2), iters=iters, adv=(0.7, 0.4, 0.0), **kw)
+
+
+def test_iterations_to_the_global_solve_aligned_two_corners_three():
+    # Sec. 5.1: under dt <= L/|V| the subdomain iteration of eq. ibvp is exact
+    # after two iterations when the velocity is aligned with the subdomain
+    # faces and after three when subdomains meet at corners.  Discretely:
+    # D2Q4 reaches the global solve (iters = 0) at K = 2, the oblique D2Q3
+    # only at K = 3, to round-off
+    for simplex, exact_at in ((False, 2), (True, 3)):
+        P0 = _two_by_two(simplex, 0)
+        f0 = np.random.default_rng(1).normal(size=P0.npop * P0.nodes)
+        ref = f0.copy()
+        oracle.transport(P0, ref)
+        errs = {}
+        for K in (exact_at - 1, exact_at):
+            g = f0.copy()
+            oracle.transport(_two_by_two(simplex, K), g)
+            errs[K] = np.abs(g - ref).max()
+        assert errs[exact_at - 1] > 1e-2, (simplex, errs)
+        assert errs[exact_at] < 1e-12, (simplex, errs)
