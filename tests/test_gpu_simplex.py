@@ -111,3 +111,28 @@ def test_simplex_errors(kin):
         with pytest.raises(kin.KinError) as ei:
             kin.kin_batch_create([ctx.ctx])
         assert ei.value.status == kin.KIN_EINVAL
+
+
+def test_async_host_copies(kin):
+    # kin_set_kinetic_async / kin_get_kinetic_async on a d + 1 context give
+    # what the synchronous copies give (no interface summaries to defer here)
+    import torch
+    w = workloads.with_(workloads.densitywave2d(seed=13, n=16, degree=2, tiles=2, dt_mult=20.0, velset=1,
+                                                precision="f32"), tiles=(2, 2))
+    out = []
+    for use_async in (False, True):
+        with kin.Context.from_workload(w) as ctx:
+            ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+            ctx.step(2)
+            h = torch.empty(ctx.info.kinetic_values, dtype=torch.float32, pin_memory=True)
+            if use_async:
+                kin.kin_get_kinetic_async(ctx.ctx, h)
+                torch.cuda.synchronize()
+                kin.kin_set_kinetic_async(ctx.ctx, h)
+                torch.cuda.synchronize()
+            else:
+                kin.kin_get_kinetic(ctx.ctx, h.numpy())
+                kin.kin_set_kinetic(ctx.ctx, h.numpy())
+            ctx.step(2)
+            out.append(ctx.get_kinetic())
+    assert np.array_equal(out[0], out[1])

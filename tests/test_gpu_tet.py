@@ -117,3 +117,27 @@ def test_bad_topology_is_rejected(kin):
         kin.TetContext(m.xyz, m.vid, m.nbr, w.subdomains(), np.zeros_like(m.wrap), w.system, kin.KIN_D3Q4,
                        w.lam, w.dt)
     assert ei.value.status == kin.KIN_EINVAL and "cycle" in str(ei.value)
+
+
+def test_async_host_copies(kin):
+    # the asynchronous host copies on a tetrahedral context give what the
+    # synchronous ones give
+    import torch
+    w = workloads.tet_densitywave(seed=14, n=4, tiles=2, velset=1, dt_mult=8.0)
+    out = []
+    for use_async in (False, True):
+        with kin.TetContext.from_workload(w) as ctx:
+            ctx.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+            ctx.step(2)
+            h = torch.empty(ctx.info.kinetic_values, dtype=torch.float32, pin_memory=True)
+            if use_async:
+                kin.kin_get_kinetic_async(ctx.ctx, h)
+                torch.cuda.synchronize()
+                kin.kin_set_kinetic_async(ctx.ctx, h)
+                torch.cuda.synchronize()
+            else:
+                kin.kin_get_kinetic(ctx.ctx, h.numpy())
+                kin.kin_set_kinetic(ctx.ctx, h.numpy())
+            ctx.step(2)
+            out.append(ctx.get_kinetic())
+    assert np.array_equal(out[0], out[1])
