@@ -149,6 +149,18 @@ def _ptr(buf):
     return buf.data_ptr(), 1 if buf.is_cuda else 0
 
 
+def _elem_check(ctx, buf, want):
+    """The C calls copy n_values elements of a fixed size (f: the context
+    precision, W: FP64); a buffer of another element size would be overrun."""
+    size = buf.itemsize if isinstance(buf, np.ndarray) else buf.element_size()
+    if size != want:
+        raise ValueError(f"expected {want}-byte values, got {buf.dtype}")
+
+
+def _f_bytes(ctx):
+    return 4 if kin_query(ctx).precision == KIN_FP32 else 8
+
+
 # torch caching-allocator hooks (PyTorch owns the device memory)
 _hooks = {}
 
@@ -194,6 +206,7 @@ def kin_create_tet(mesh: kin_tetmesh, model: kin_model, dt: float, opts: kin_opt
 
 
 def kin_set_state(ctx, W, n_values=None):
+    _elem_check(ctx, W, 8)
     p, dev = _ptr(W)
     n = W.size if isinstance(W, np.ndarray) else W.numel()
     _check(ctx, load_library().kin_set_state(ctx, p, n if n_values is None else n_values, dev))
@@ -206,26 +219,31 @@ def kin_set_boundary(ctx, axis, side, W):
 
 
 def kin_set_kinetic(ctx, f, n_values=None):
+    _elem_check(ctx, f, _f_bytes(ctx))
     p, dev = _ptr(f)
     n = f.size if isinstance(f, np.ndarray) else f.numel()
     _check(ctx, load_library().kin_set_kinetic(ctx, p, n if n_values is None else n_values, dev))
 
 
-def _host_ptr(a):
-    """Address and size of a page-locked host torch tensor (the async copies
-    need one; a pageable numpy array would make the copy synchronous)."""
-    if not (hasattr(a, "is_pinned") and a.is_pinned()):
-        raise ValueError("the asynchronous host copies take a page-locked torch tensor")
+def _host_ptr(ctx, a):
+    """Address and size of a page-locked host torch tensor whose element size
+    is the context's (the async copies move n_values elements of the context
+    precision; a pageable numpy array would make the copy synchronous)."""
+    if not (hasattr(a, "is_pinned") and a.is_pinned() and a.is_contiguous()):
+        raise ValueError("the asynchronous host copies take a contiguous page-locked torch tensor")
+    want = 4 if kin_query(ctx).precision == KIN_FP32 else 8
+    if a.element_size() != want:
+        raise ValueError(f"the context holds {want}-byte values; got a {a.dtype} tensor")
     return ctypes.c_void_p(a.data_ptr()), a.numel()
 
 
 def kin_set_kinetic_async(ctx, f, stream=None):
-    p, n = _host_ptr(f)
+    p, n = _host_ptr(ctx, f)
     _check(ctx, load_library().kin_set_kinetic_async(ctx, p, n, stream))
 
 
 def kin_get_kinetic_async(ctx, f, stream=None):
-    p, n = _host_ptr(f)
+    p, n = _host_ptr(ctx, f)
     _check(ctx, load_library().kin_get_kinetic_async(ctx, p, n, stream))
 
 
@@ -234,12 +252,14 @@ def kin_step(ctx, nsteps: int):
 
 
 def kin_get_state(ctx, W, n_values=None):
+    _elem_check(ctx, W, 8)
     p, dev = _ptr(W)
     n = W.size if isinstance(W, np.ndarray) else W.numel()
     _check(ctx, load_library().kin_get_state(ctx, p, n if n_values is None else n_values, dev))
 
 
 def kin_get_kinetic(ctx, f, n_values=None):
+    _elem_check(ctx, f, _f_bytes(ctx))
     p, dev = _ptr(f)
     n = f.size if isinstance(f, np.ndarray) else f.numel()
     _check(ctx, load_library().kin_get_kinetic(ctx, p, n if n_values is None else n_values, dev))
