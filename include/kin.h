@@ -328,6 +328,13 @@ kin_status kin_step_noalloc(const kin_mesh* mesh, const kin_model* model, int de
  * of the batch (NULL = a stream the batch creates and owns; the legacy
  * default stream cannot hold the captured graphs); work already queued on a
  * member's stream runs before the batch step, and later work on it after.
+ * That second order is lazy: a batch step records an event per member, and
+ * the member's next call of this library (on its own stream, or on the
+ * stream an asynchronous copy names) waits for that event, so a stream that
+ * several contexts share is held up only by their own steps.  A new batch of
+ * members still in flight in another batch waits for them the same way; a
+ * member's own stream, used directly (not through this library), is not
+ * ordered after the step until kin_sync or another call on the member.
  * Stepping a member alone while it is in a batch invalidates the batch
  * (KIN_ESTATE on the next kin_batch_step).  A member's kin_set_boundary
  * applies from the next batch step on.  Errors: KIN_EINVAL (bad

@@ -82,6 +82,8 @@ struct kin_ctx {
     std::vector<double> tvol;         // host: cell volumes, for the mass diagnostic
     bool have_state = false;
     bool sum_stale = false;           // f was replaced without recomputing the interface summaries
+    cudaEvent_t after_batch = nullptr;   // recorded on a batch's stream after its last step of this context
+    bool wait_batch = false;          // the context's next work must wait for after_batch
     long long steps_done = 0;
     bool poisoned = false;
     std::string err;
@@ -139,6 +141,8 @@ static kin_status dev_alloc(kin_ctx* c, size_t bytes, void** out)
 
 static void release_all(kin_ctx* c)
 {
+    if (c->after_batch) cudaEventDestroy(c->after_batch);
+    c->after_batch = nullptr;
     for (auto& b : c->blocks) {
         if (c->dealloc) c->dealloc(b.first, b.second, (void*)c->stream, c->alloc_user);
         else cudaFree(b.first);
@@ -280,16 +284,22 @@ static Inst make_inst(const kin_ctx* c, int mode)
     return I;
 }
 
+// Status of a device error word value h.
+static kin_status errword_status(kin_ctx* c, int h)
+{
+    if (h & kErrLoadTimeout)
+        return fail(c, KIN_ETIMEOUT, "a thread block gave up waiting for its bulk loads (bounded wait ran out)");
+    if (h) return fail(c, KIN_ETIMEOUT, "device error word 0x%x", h);
+    return KIN_OK;
+}
+
 // Read the device error word (after the stream has been synchronised).
 static kin_status check_errword(kin_ctx* c)
 {
     int h = 0;
     KIN_CUDA(c, cudaMemcpyAsync(&h, c->errword, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     KIN_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (h & kErrLoadTimeout)
-        return fail(c, KIN_ETIMEOUT, "a thread block gave up waiting for its bulk loads (bounded wait ran out)");
-    if (h) return fail(c, KIN_ETIMEOUT, "device error word 0x%x", h);
-    return KIN_OK;
+    return errword_status(c, h);
 }
 
 // Work items of one tile: (population, line) pairs per axis and nodes.
@@ -422,6 +432,18 @@ static kin_status check_usable(const kin_ctx* c)
     if (!c) return KIN_EINVAL;
     if (c->poisoned) return KIN_ESTATE;
     return KIN_OK;
+}
+
+// A batch step runs a context's work on the batch's stream.  The context's
+// own stream (or a stream the caller names for a copy) waits for it only
+// when the context is next used, so that a stream several contexts share is
+// not held up by a batch step of other contexts.
+static cudaError_t order_after_batch(kin_ctx* c, cudaStream_t s)
+{
+    if (!c->wait_batch) return cudaSuccess;
+    const cudaError_t e = cudaStreamWaitEvent(s, c->after_batch, 0);
+    if (e == cudaSuccess && s == c->stream) c->wait_batch = false;
+    return e;
 }
 
 // ---- d + 1 velocity sets: launch arguments and one step ----
@@ -1128,6 +1150,7 @@ kin_status kin_set_state(kin_ctx* c, const double* W, size_t n_values, int on_de
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, c->stream));
     if (!W) return fail(c, KIN_EINVAL, "W is NULL");
     if (n_values != (size_t)c->m * c->nodes)
         return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->m * c->nodes, n_values);
@@ -1160,6 +1183,7 @@ kin_status kin_set_kinetic(kin_ctx* c, const void* f, size_t n_values, int on_de
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, c->stream));
     if (!f) return fail(c, KIN_EINVAL, "f is NULL");
     if (n_values != (size_t)c->npop * c->nodes)
         return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
@@ -1182,6 +1206,7 @@ kin_status kin_set_kinetic_async(kin_ctx* c, const void* f, size_t n_values, voi
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, stream ? (cudaStream_t)stream : c->stream));
     if (!f) return fail(c, KIN_EINVAL, "f is NULL");
     if (n_values != (size_t)c->npop * c->nodes)
         return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
@@ -1198,6 +1223,7 @@ kin_status kin_get_kinetic_async(kin_ctx* c, void* f, size_t n_values, void* str
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, stream ? (cudaStream_t)stream : c->stream));
     if (!f) return fail(c, KIN_EINVAL, "f is NULL");
     if (n_values != (size_t)c->npop * c->nodes)
         return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
@@ -1221,6 +1247,7 @@ kin_status kin_set_boundary(kin_ctx* c, int axis, int side, const double* W, siz
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, c->stream));
     if (c->tet) return fail(c, KIN_EINVAL, "tetrahedral meshes are periodic: no boundary faces");
     if (axis < 0 || axis >= c->dim || !c->inflow[axis])
         return fail(c, KIN_EINVAL, "axis %d is not an inflow axis", axis);
@@ -1252,6 +1279,7 @@ kin_status kin_step(kin_ctx* c, int nsteps)
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, c->stream));
     if (nsteps < 0) return fail(c, KIN_EINVAL, "nsteps must be >= 0");
     if (!c->have_state) return fail(c, KIN_ESTATE, "no state: call kin_set_state or kin_set_kinetic first");
     if (const char* face = missing_boundary(c))
@@ -1273,6 +1301,7 @@ kin_status kin_get_state(kin_ctx* c, double* W, size_t n_values, int on_device)
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, c->stream));
     if (!W) return fail(c, KIN_EINVAL, "W is NULL");
     if (n_values != (size_t)c->m * c->nodes)
         return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->m * c->nodes, n_values);
@@ -1292,6 +1321,7 @@ kin_status kin_get_kinetic(kin_ctx* c, void* f, size_t n_values, int on_device)
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, c->stream));
     if (!f) return fail(c, KIN_EINVAL, "f is NULL");
     if (n_values != (size_t)c->npop * c->nodes)
         return fail(c, KIN_EINVAL, "expected %zu values, got %zu", (size_t)c->npop * c->nodes, n_values);
@@ -1309,6 +1339,7 @@ kin_status kin_diag(kin_ctx* c, double* mass_per_var, double* next_defect, doubl
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, c->stream));
     if (!c->have_state) return fail(c, KIN_ESTATE, "no state has been set");
     if ((next_defect || iter_residual) && (c->inflow[0] || c->inflow[1] || c->inflow[2]))
         return fail(c, KIN_EINVAL, "next_defect and iter_residual are not available with inflow axes");
@@ -1392,6 +1423,7 @@ kin_status kin_sync(kin_ctx* c)
 {
     kin_status st = check_usable(c);
     if (st) return st;
+    KIN_CUDA(c, order_after_batch(c, c->stream));
     KIN_CUDA(c, cudaStreamSynchronize(c->stream));
     return check_errword(c);
 }
@@ -1425,6 +1457,7 @@ kin_status kin_query(const kin_ctx* c, kin_info* info)
 kin_status kin_destroy(kin_ctx* c)
 {
     if (!c) return KIN_OK;
+    if (c->wait_batch) cudaEventSynchronize(c->after_batch);
     cudaStreamSynchronize(c->stream);
     release_all(c);
     delete c;
@@ -1461,7 +1494,7 @@ struct kin_batch {
     std::vector<Group> groups;        // groups[0] is the mixed launch when nmixed > 0
     Group mixed;                      // members of the one-launch mixed-degree kernel
     int nmixed = 0;
-    std::vector<void*> dev;           // device allocations of the batch
+    void* arena = nullptr;            // one stream-ordered device allocation: launch records and work lists
     std::vector<cudaEvent_t> ev_member;
     cudaEvent_t ev_done = nullptr;
     bool direct = false;              // enqueue the launches per step instead of replaying graphs
@@ -1496,8 +1529,10 @@ static void batch_release(kin_batch* b)
     for (auto e : b->ev_member)
         if (e) cudaEventDestroy(e);
     if (b->ev_done) cudaEventDestroy(b->ev_done);
-    for (void* p : b->dev) cudaFree(p);
-    b->dev.clear();
+    // stream-ordered free: no device-wide synchronisation while other
+    // streams run (the batch's work on its stream finishes first)
+    if (b->arena) cudaFreeAsync(b->arena, b->stream);
+    b->arena = nullptr;
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     b->stream = nullptr;
 }
@@ -1665,6 +1700,19 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
     int dev = 0, nsm = 1;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // every group's launch records and work list, staged on the host and
+    // copied into one device arena (offsets 256-byte aligned)
+    std::vector<unsigned char> stage;
+    auto place = [&](const void* src, size_t bytes) {
+        const size_t off = (stage.size() + 255) / 256 * 256;
+        stage.resize(off + bytes);
+        memcpy(stage.data() + off, src, bytes);
+        return off;
+    };
+    struct Offs {
+        size_t insts[2], prep[2], work;
+    };
+    std::vector<Offs> offs(b->groups.size());
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         auto& g = b->groups[gi];
         if (e != cudaSuccess) break;
@@ -1705,25 +1753,25 @@ extern "C" kin_status kin_batch_create_ex(kin_ctx* const* members, int count, vo
         int occ = 1;
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g.fn, g.threads, g.smem);
         g.grid = (int)std::min<long long>(g.nwork, (long long)std::max(occ, 1) * nsm);
-        for (int q = 0; q < 2 && e == cudaSuccess; ++q)
-            for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
-                const std::vector<Inst>& src = kind == 0 ? h[q] : hp[q];
-                void* p = nullptr;
-                e = cudaMalloc(&p, sizeof(Inst) * src.size());
-                if (e == cudaSuccess) {
-                    b->dev.push_back(p);
-                    (kind == 0 ? g.insts[q] : g.prep[q]) = (Inst*)p;
-                    e = cudaMemcpy(p, src.data(), sizeof(Inst) * src.size(), cudaMemcpyHostToDevice);
-                }
+        for (int q = 0; q < 2; ++q) {
+            offs[gi].insts[q] = place(h[q].data(), sizeof(Inst) * h[q].size());
+            offs[gi].prep[q] = place(hp[q].data(), sizeof(Inst) * hp[q].size());
+        }
+        offs[gi].work = place(work.data(), sizeof(int2) * work.size());
+    }
+    if (e == cudaSuccess && !stage.empty()) {
+        e = cudaMallocAsync(&b->arena, stage.size(), b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->arena, stage.data(), stage.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // the staging vector goes away
+        for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+            auto& g = b->groups[gi];
+            unsigned char* base = static_cast<unsigned char*>(b->arena);
+            for (int q = 0; q < 2; ++q) {
+                g.insts[q] = reinterpret_cast<Inst*>(base + offs[gi].insts[q]);
+                g.prep[q] = reinterpret_cast<Inst*>(base + offs[gi].prep[q]);
             }
-        if (e == cudaSuccess) {
-            void* p = nullptr;
-            e = cudaMalloc(&p, sizeof(int2) * work.size());
-            if (e == cudaSuccess) {
-                b->dev.push_back(p);
-                g.work = (int2*)p;
-                e = cudaMemcpy(p, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice);
-            }
+            g.work = reinterpret_cast<int2*>(base + offs[gi].work);
         }
     }
     b->ev_member.assign(count, nullptr);
@@ -1760,10 +1808,18 @@ extern "C" kin_status kin_batch_step(kin_batch* b, int nsteps)
             return batch_fail(b, KIN_ESTATE, "member %zu has an inflow face without a boundary state", i);
     }
     if (nsteps == 0) return KIN_OK;
+    // order the step after each member's earlier work: a member whose last
+    // work was a batch step waits for that step's event (no call since then
+    // enqueued on its own stream); any other member waits for its stream
     cudaError_t e = cudaSuccess;
     for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i) {
-        e = cudaEventRecord(b->ev_member[i], b->members[i]->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_member[i], 0);
+        kin_ctx* c = b->members[i];
+        if (c->wait_batch) {
+            e = cudaStreamWaitEvent(b->stream, c->after_batch, 0);
+        } else {
+            e = cudaEventRecord(b->ev_member[i], c->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_member[i], 0);
+        }
     }
     // members whose f was replaced by kin_set_kinetic_async: one summaries
     // pass over every member, one launch per kernel type, before the step
@@ -1790,8 +1846,13 @@ extern "C" kin_status kin_batch_step(kin_batch* b, int nsteps)
         }
     }
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_done, b->stream);
-    for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i)
-        e = cudaStreamWaitEvent(b->members[i]->stream, b->ev_done, 0);
+    // each member's later work waits for this step when the member is next used
+    for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i) {
+        kin_ctx* c = b->members[i];
+        if (!c->after_batch) e = cudaEventCreateWithFlags(&c->after_batch, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(c->after_batch, b->stream);
+        if (e == cudaSuccess) c->wait_batch = true;
+    }
     if (e != cudaSuccess) return batch_fail(b, KIN_ECUDA, "batch step failed: %s", cudaGetErrorString(e));
     for (auto* c : b->members) {
         if (nsteps & 1) c->cur ^= 1;
@@ -1805,8 +1866,15 @@ extern "C" kin_status kin_batch_sync(kin_batch* b)
     if (!b) return KIN_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return batch_fail(b, KIN_ECUDA, "batch sync failed: %s", cudaGetErrorString(e));
+    // the error words are read on the batch's stream: a member's own stream
+    // may be shared with, and busy on behalf of, contexts outside the batch
+    std::vector<int> h(b->members.size(), 0);
+    for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(&h[i], b->members[i]->errword, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, KIN_ECUDA, "batch sync failed: %s", cudaGetErrorString(e));
     for (size_t i = 0; i < b->members.size(); ++i) {
-        kin_status st = check_errword(b->members[i]);
+        kin_status st = errword_status(b->members[i], h[i]);
         if (st) return batch_fail(b, st, "member %zu: %s", i, b->members[i]->err.c_str());
     }
     return KIN_OK;

@@ -82,23 +82,31 @@ class Server:
         """requests: objects with rid, arrival (s), steps; workload_of(r) -> Workload.
         Returns the Served records in request order.
 
-        Each round enqueues one chunk of steps for the active batch, admits
-        the requests that have arrived meanwhile (context creation and
-        initial state run on the new contexts' own streams while the chunk
-        runs), then waits for the chunk, retires finished requests and folds
-        the admitted ones into the next batch.  After the run,
-        self.device_busy_s holds the device time spent inside chunks."""
+        The loop keeps one chunk of steps queued behind the one that runs.
+        Each round enqueues the next chunk for the active set, then waits
+        for the previous chunk, reads back and retires the requests that
+        finished with it and admits the requests that have arrived (context
+        creation and initial state on a separate, high-priority stream), all
+        while the new chunk runs.  A change of membership makes a new batch
+        on the other of two run streams; it is ordered after the running
+        chunk through its continuing members' events.  After the run,
+        self.device_busy_s holds the device time covered by chunks."""
         import torch
+
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         records = {r.rid: Served(r.rid, r.arrival) for r in requests}
         active = []            # [record, context, remaining steps, bytes]
         used = 0.0
-        batch = None
-        # the batch runs on the server's stream; new contexts are created and
-        # loaded on a second stream, so admission overlaps the running chunk
-        run_stream = torch.cuda.Stream()
-        adm_stream = torch.cuda.Stream()
-        chunks = []            # (start, end) events of every chunk on the run stream
+        run_streams = (torch.cuda.Stream(), torch.cuda.Stream())
+        which = 0              # run stream of the next batch
+        try:
+            lo, hi = torch.cuda.Stream.priority_range()
+            adm_stream = torch.cuda.Stream(priority=min(lo, hi))     # the highest priority
+        except (AttributeError, RuntimeError):
+            adm_stream = torch.cuda.Stream()
+        origin = torch.cuda.Event(enable_timing=True)
+        origin.record(run_streams[0])
+        chunks = []            # (start, end) events of every chunk
         self.peak_bytes = 0    # most device bytes held by admitted requests at once
         t0 = clock()
 
@@ -124,54 +132,62 @@ class Server:
                 new.append([rec, ctx, r.steps, ctx.info.device_bytes])
             return new
 
-        while pending or active:
-            k = 0
+        def retire(done):
+            nonlocal used
+            for rec, ctx, _, nbytes in done:
+                W = self._read_result(ctx)
+                rec.finished = clock() - t0
+                if self.keep_results:
+                    rec.result = W
+                ctx.close()
+                used -= nbytes
+
+        batch = None           # batch of the active set
+        inflight = None        # (end event, finished entries, batch) of the chunk queued last
+        while pending or active or inflight is not None:
+            queued = None
             if active:
                 if batch is None:
                     # membership changes every few chunks: direct launches, no graph capture
-                    batch = Batch([a[1] for a in active], stream=run_stream.cuda_stream, graphs=False,
+                    run = run_streams[which]
+                    batch = Batch([a[1] for a in active], stream=run.cuda_stream, graphs=False,
                                   mixed=self.mixed)
                 k = min(self.chunk, min(a[2] for a in active))
                 ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                ev[0].record(run_stream)
+                ev[0].record(run)
                 batch.step(k)                              # asynchronous
-                ev[1].record(run_stream)
+                ev[1].record(run)
                 chunks.append(ev)
-            new = admit(clock() - t0)                      # overlaps the chunk
-            if not active and not new:
-                if pending:
-                    time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
-                continue
-            still = []
-            if active:
-                batch.sync()
                 for a in active:
                     a[2] -= k
-                    if a[2] == 0:
-                        rec, ctx = a[0], a[1]
-                        W = self._read_result(ctx)
-                        rec.finished = clock() - t0
-                        if self.keep_results:
-                            rec.result = W
-                        used -= a[3]
-                    else:
-                        still.append(a)
-                if len(still) != len(active) or new:
-                    batch.close()
-                    batch = None
-                for a in active:
-                    if a[2] == 0:
-                        a[1].close()
-            elif new and batch is not None:
-                batch.close()
-                batch = None
-            active = still + new
+                queued = (ev[1], [a for a in active if a[2] == 0], batch)
+                active = [a for a in active if a[2] > 0]
+            if inflight is not None:
+                inflight[0].synchronize()                  # the previous chunk; the queued one runs
+                if inflight[2] is not batch:               # superseded: its stream is idle
+                    inflight[2].sync()                     # checks the members' error words
+                    inflight[2].close()                    # before its finished members go
+                retire(inflight[1])
+            new = admit(clock() - t0)
+            if queued is not None and (queued[1] or new) and batch is queued[2]:
+                batch = None                               # the next chunk needs a new batch
+                which ^= 1
+            active = active + new
+            inflight = queued
+            if not active and inflight is None and pending:
+                time.sleep(max(0.0, pending[0].arrival - (clock() - t0)))
         if batch is not None:
             batch.close()
         torch.cuda.synchronize()
-        # device time spent inside chunks (the rest of the makespan is host
-        # work between chunks, ramp-up and tail)
-        self.device_busy_s = sum(a.elapsed_time(b) for a, b in chunks) * 1e-3
+        # device time covered by chunks (the union of their intervals; the
+        # rest of the makespan is host work between chunks, ramp-up and tail)
+        spans = sorted((origin.elapsed_time(a), origin.elapsed_time(b)) for a, b in chunks)
+        busy, end = 0.0, float("-inf")
+        for a, b in spans:
+            if b > end:
+                busy += b - max(a, end)
+                end = b
+        self.device_busy_s = busy * 1e-3
         return [records[r.rid] for r in requests]
 
 

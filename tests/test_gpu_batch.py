@@ -256,3 +256,41 @@ def test_async_set_then_step_equals_synchronous(kin):
             out.append((c.get_kinetic(), dfc))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_lazy_ordering_across_batches_and_a_shared_stream(kin):
+    """Members sharing one stream, stepped by a batch on one stream and then,
+    with nothing synchronised, by a new batch of the same members on another:
+    the second batch is ordered after the first through the members' events,
+    and a member's own later calls (a step, a read) wait for the second."""
+    import torch
+    ws, blocks = _mix()
+    ws, blocks = ws[:5], blocks[:5]
+    alone = []
+    for w, b in zip(ws, blocks):
+        with _ctx(kin, w, b) as c:
+            c.step(8)
+            alone.append(c.get_kinetic())
+    shared = torch.cuda.Stream()
+    ctxs = []
+    for w, b in zip(ws, blocks):
+        kw = {} if b is None else {"block": b}
+        c = kin.Context.from_workload(w, stream=shared.cuda_stream, **kw)
+        c.set_state(np.ascontiguousarray(w.W0.reshape(-1)))
+        ctxs.append(c)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    b1 = kin.Batch(ctxs, stream=s1.cuda_stream, graphs=False)
+    b1.step(4)
+    b2 = kin.Batch(ctxs, stream=s2.cuda_stream)
+    b2.step(3)
+    ctxs[0].step(1)                      # on the shared stream, after the second batch
+    for i, (c, want) in enumerate(zip(ctxs, alone)):
+        if i > 0:
+            c.step(1)
+        assert np.array_equal(c.get_kinetic(), want), i
+        assert kin.kin_query(c.ctx).steps_done == 8
+    b2.sync()
+    b1.close()
+    b2.close()
+    for c in ctxs:
+        c.close()
