@@ -117,7 +117,7 @@ class Server:
                 r = pending[0]
                 w = workload_of(r)
                 need = state_bytes_estimate(w)
-                if used + need > self.budget and (active or new):
+                if used > 0 and used + need > self.budget:
                     break                                  # wait for memory to free up
                 pending.popleft()
                 ctx = Context.from_workload(w, precision=KIN_FP32, torch_alloc=self.torch_alloc,
