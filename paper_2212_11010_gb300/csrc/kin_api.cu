@@ -1808,18 +1808,18 @@ extern "C" kin_status kin_batch_step(kin_batch* b, int nsteps)
             return batch_fail(b, KIN_ESTATE, "member %zu has an inflow face without a boundary state", i);
     }
     if (nsteps == 0) return KIN_OK;
-    // order the step after each member's earlier work: a member whose last
-    // work was a batch step waits for that step's event (no call since then
-    // enqueued on its own stream); any other member waits for its stream
+    // order the step after each member's earlier work: the work queued on
+    // its stream (once per distinct stream) and, when its last step was a
+    // batch step on another stream, that step
     cudaError_t e = cudaSuccess;
+    std::vector<cudaStream_t> seen;
     for (size_t i = 0; i < b->members.size() && e == cudaSuccess; ++i) {
         kin_ctx* c = b->members[i];
-        if (c->wait_batch) {
-            e = cudaStreamWaitEvent(b->stream, c->after_batch, 0);
-        } else {
-            e = cudaEventRecord(b->ev_member[i], c->stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_member[i], 0);
-        }
+        if (c->wait_batch) e = cudaStreamWaitEvent(b->stream, c->after_batch, 0);
+        if (e != cudaSuccess || std::find(seen.begin(), seen.end(), c->stream) != seen.end()) continue;
+        seen.push_back(c->stream);
+        e = cudaEventRecord(b->ev_member[i], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_member[i], 0);
     }
     // members whose f was replaced by kin_set_kinetic_async: one summaries
     // pass over every member, one launch per kernel type, before the step
