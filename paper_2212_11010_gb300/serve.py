@@ -152,7 +152,11 @@ class Server:
                     run = run_streams[which]
                     batch = Batch([a[1] for a in active], stream=run.cuda_stream, graphs=False,
                                   mixed=self.mixed)
-                k = min(self.chunk, min(a[2] for a in active))
+                # chunks bound the wait of a pending request; with none
+                # pending, a chunk runs up to the next finish
+                k = min(a[2] for a in active)
+                if pending:
+                    k = min(k, self.chunk)
                 ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                 ev[0].record(run)
                 batch.step(k)                              # asynchronous
@@ -165,7 +169,7 @@ class Server:
             if inflight is not None:
                 inflight[0].synchronize()                  # the previous chunk; the queued one runs
                 if inflight[2] is not batch:               # superseded: its stream is idle
-                    inflight[2].sync()                     # checks the members' error words
+                    # (a member's device error word is checked when its result is read)
                     inflight[2].close()                    # before its finished members go
                 retire(inflight[1])
             new = admit(clock() - t0)

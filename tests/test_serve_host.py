@@ -183,7 +183,15 @@ def test_serving_loop_bookkeeping(world, seed, count, chunk, budget_requests):
     need = [_workload(r).bytes for r in reqs]
     budget = budget_requests * max(need)
     server = serve.Server(budget_bytes=budget, chunk_steps=chunk, mixed=False, pinned_results=False)
-    recs = server.run(reqs, _workload)
+    # a clock that advances 0.1 ms per reading: the interleaving of arrivals
+    # and loop rounds is the same on every run
+    now = [0.0]
+
+    def clock():
+        now[0] += 1e-4
+        return now[0]
+
+    recs = server.run(reqs, _workload, clock=clock)
     for r, rec in zip(reqs, recs):
         assert rec.finished is not None and rec.admitted is not None
         assert rec.admitted >= r.arrival - 1e-9
