@@ -92,7 +92,7 @@ cudaError_t sx_launch_init(const SxArgs& a, const double* W, int prec, cudaStrea
 
 // ---- tetrahedral meshes (kin_tet.cu) ----
 constexpr int kTetRec = 24;       // coefficient slots per (velocity, cell)
-constexpr int kTetSweepThreads = 512;
+constexpr int kTetSweepThreads = 640;
 
 struct TetSetupArgs {
     int ncells, nvel;

@@ -178,7 +178,7 @@ __device__ __forceinline__ void store4(T* p, const T (&u)[4])
 // round of loads (its cells' records and neighbour values, issued together)
 // rather than for a chain of dependent ones.
 template <typename T>
-__global__ void __launch_bounds__(kTetSweepThreads) tet_sweep_kernel(TetArgs A, const T* __restrict__ prev, T* cur)
+__global__ void __launch_bounds__(kTetSweepThreads, 2) tet_sweep_kernel(TetArgs A, const T* __restrict__ prev, T* cur)
 {
     const int s = blockIdx.x, k = blockIdx.y;
     const int* __restrict__ order = A.order + (size_t)k * A.ncells;
