@@ -1045,8 +1045,9 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
         }
     }
     // inflow face vertices per (velocity, position in its order): the
-    // neighbour's node, doubled, + 1 when the face is a subdomain interface
-    std::vector<int> fref((size_t)c->nvel * n * 12, 0);
+    // neighbour's node, doubled, + 1 when the face is a subdomain interface;
+    // -1 on the faces that are not inflow faces
+    std::vector<int> fref((size_t)c->nvel * n * 12, -1);
     for (int k = 0; k < c->nvel; ++k)
         for (int q = 0; q < n; ++q) {
             const int cc = order[(size_t)k * n + q];

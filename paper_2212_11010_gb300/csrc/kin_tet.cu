@@ -172,11 +172,12 @@ __device__ __forceinline__ void store4(T* p, const T (&u)[4])
 // c cells offers c m independent solves.  The inflow face vertices are
 // resolved ahead of time, per position of the velocity's level order:
 // fref = 2 (global node) + 1 when the face is a subdomain interface (the
-// value comes from the previous iterate), + 0 otherwise (the current one).
-// A thread's first pair of a level has its cell loaded two levels ahead and
-// its face references and f^n one level ahead, so a level waits for one
-// round of loads (its cells' records and neighbour values, issued together)
-// rather than for a chain of dependent ones.
+// value comes from the previous iterate), + 0 otherwise (the current one),
+// and -1 on the faces that are not inflow faces.  A thread's first pair of
+// a level has its cell and face references loaded during the level before,
+// so a level waits for one round of loads (the cell's f^n and record and the
+// neighbour values, issued together: the face types come from the
+// references) rather than for a chain of dependent ones.
 template <typename T>
 __global__ void __launch_bounds__(kTetSweepThreads, 2) tet_sweep_kernel(TetArgs A, const T* __restrict__ prev, T* cur)
 {
@@ -208,8 +209,10 @@ __global__ void __launch_bounds__(kTetSweepThreads, 2) tet_sweep_kernel(TetArgs 
         for (int i = 0; i < 4; ++i) rhs[i] = m20 * (sum + du[i]);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
+            // (the face type comes from the references, already in registers,
+            // so the neighbour loads need not wait for the record)
+            if (nr[a * 3] < 0) continue;
             const T ca = rec[17 + a];
-            if (ca == T(0)) continue;
             // the neighbour's values at this cell's face vertices (j != a, ascending)
             T g[4] = {T(0), T(0), T(0), T(0)};
             T gs = T(0);
