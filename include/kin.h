@@ -353,8 +353,15 @@ kin_status kin_batch_create_ex(kin_ctx* const* members, int count, void* stream,
 /* Launches of this library per batch step, and how many members share the
  * mixed-degree launch (either pointer may be NULL). */
 kin_status kin_batch_info(const kin_batch* batch, int* launches_per_step, int* mixed_members);
+/* Enqueue nsteps steps of every member on the batch's stream (asynchronous).
+ * KIN_ESTATE if a member is poisoned, was stepped outside the batch or lacks
+ * a boundary state on an inflow face; KIN_ECUDA on a launch error. */
 kin_status kin_batch_step(kin_batch* batch, int nsteps);
+/* Wait for the batch's stream, then read every member's device error word
+ * (on the batch's stream): KIN_ETIMEOUT names the first member whose bounded
+ * device wait ran out. */
 kin_status kin_batch_sync(kin_batch* batch);
+/* Wait for the batch's stream and free the batch; the members stay. */
 kin_status kin_batch_destroy(kin_batch* batch);
 /* Message of the last error of this batch (or of the last failed
  * kin_batch_create on this thread when batch is NULL); never NULL. */
