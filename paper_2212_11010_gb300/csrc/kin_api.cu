@@ -77,7 +77,7 @@ struct kin_ctx {
     int* torder = nullptr;            // [velocity][cells]
     int* tlstart = nullptr;           // [velocity][nsub + 1]
     int* tbounds = nullptr;           // level boundaries
-    int* tfref = nullptr;             // [velocity][position][4][3] inflow face vertex references
+    int* tfref = nullptr;             // [velocity][position][4] packed inflow face references
     void* titer[2] = {nullptr, nullptr};   // subdomain iterates
     std::vector<double> tvol;         // host: cell volumes, for the mass diagnostic
     bool have_state = false;
@@ -1044,18 +1044,21 @@ kin_status kin_create_tet(const kin_tetmesh* mesh, const kin_model* model, doubl
             bounds.push_back(pos);
         }
     }
-    // inflow face vertices per (velocity, position in its order): the
-    // neighbour's node, doubled, + 1 when the face is a subdomain interface;
-    // -1 on the faces that are not inflow faces
-    std::vector<int> fref((size_t)c->nvel * n * 12, -1);
+    // inflow faces per (velocity, position in its order), one word each:
+    // the neighbour cell R << 7, the neighbour's local index (2 bits) of
+    // each of the face's three vertices at bits 5, 3 and 1, and bit 0 set
+    // when the face is a subdomain interface; -1 on the faces that are not
+    // inflow faces (R < 2^24 by the cell-count check above)
+    std::vector<int> fref((size_t)c->nvel * n * 4, -1);
     for (int k = 0; k < c->nvel; ++k)
         for (int q = 0; q < n; ++q) {
             const int cc = order[(size_t)k * n + q];
             for (int a = 0; a < 4; ++a) {
                 if (((ftype[(size_t)k * n + cc] >> (2 * a)) & 3) != 1) continue;
-                for (int jj = 0; jj < 3; ++jj)
-                    fref[((size_t)k * n + q) * 12 + a * 3 + jj] =
-                        2 * fnodes[(size_t)cc * 12 + a * 3 + jj] + ((iface[cc] >> a) & 1);
+                const int R = fnodes[(size_t)cc * 12 + a * 3] / 4;
+                int wd = (R << 7) | ((iface[cc] >> a) & 1);
+                for (int jj = 0; jj < 3; ++jj) wd |= (fnodes[(size_t)cc * 12 + a * 3 + jj] & 3) << (5 - 2 * jj);
+                fref[((size_t)k * n + q) * 4 + a] = wd;
             }
         }
 

@@ -112,8 +112,8 @@ struct TetArgs {
     const int* order;             // [velocity][ncells]: cells by subdomain, then breadth-first
     const int* lstart;            // [velocity][nsub + 1]: first level index of each subdomain in bounds
     const int* bounds;            // level l of the order holds positions [bounds[l], bounds[l + 1])
-    const int* fref;              // [velocity][position][face a][3]: 2 (neighbour's node) + 1 at an interface;
-                                  // -1 on a face that is not an inflow face
+    const int* fref;              // [velocity][position][face a]: neighbour cell << 7 | its local index of
+                                  // the face's vertices (bits 5, 3, 1) | 1 at an interface; -1 if not inflow
     void* f;                      // T [pop][cell][4]
     double lambda, gamma, omega, mu;
     double adv[3];

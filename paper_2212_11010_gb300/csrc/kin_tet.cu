@@ -169,12 +169,14 @@ __device__ __forceinline__ void store4(T* p, const T (&u)[4])
 
 // Every thread takes one (cell, variable) pair of the level: the m threads
 // of a cell read the same coefficient record (one broadcast), and a level of
-// c cells offers c m independent solves.  The inflow face vertices are
-// resolved ahead of time, per position of the velocity's level order:
-// fref = 2 (global node) + 1 when the face is a subdomain interface (the
-// value comes from the previous iterate), + 0 otherwise (the current one),
-// and -1 on the faces that are not inflow faces.  A thread's first pair of
-// a level has its cell and face references loaded during the level before,
+// c cells offers c m independent solves.  The inflow faces are resolved
+// ahead of time, per position of the velocity's level order, one word per
+// face: the neighbour cell R << 7, the neighbour's local index of each of
+// the face's three vertices (2 bits at bits 5, 3, 1), and bit 0 set when the
+// face is a subdomain interface (the value comes from the previous iterate,
+// else from the current one); -1 on the faces that are not inflow faces.
+// A thread's first pair of a level has its cell and face references loaded
+// during the level before,
 // so a level waits for one round of loads (the cell's f^n and record and the
 // neighbour values, issued together: the face types come from the
 // references) rather than for a chain of dependent ones.
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kTetSweepThreads, 2) tet_sweep_kernel(TetArgs 
 {
     const int s = blockIdx.x, k = blockIdx.y;
     const int* __restrict__ order = A.order + (size_t)k * A.ncells;
-    const int* __restrict__ fref = A.fref + (size_t)k * A.ncells * 12;
+    const int* __restrict__ fref = A.fref + (size_t)k * A.ncells * 4;
     const int lb = A.lstart[k * (A.nsub + 1) + s], le = A.lstart[k * (A.nsub + 1) + s + 1];
     const T* __restrict__ coef = static_cast<const T*>(A.coef) + (size_t)k * A.ncells * kTetRec;
     const T* __restrict__ fn = static_cast<const T*>(A.f);
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kTetSweepThreads, 2) tet_sweep_kernel(TetArgs 
     const int m = A.m;
     const int tid = threadIdx.x, nt = blockDim.x;
 
-    auto solve = [&](int pos, int v, int c, const int (&nr)[12]) {
+    auto solve = [&](int pos, int v, int c, const int4 nr) {
         const T* rec = coef + (size_t)pos * kTetRec;
         const long long pop = (long long)(k * m + v) * nodes;
         T u[4];
@@ -207,12 +209,15 @@ __global__ void __launch_bounds__(kTetSweepThreads, 2) tet_sweep_kernel(TetArgs 
         T rhs[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) rhs[i] = m20 * (sum + du[i]);
+        const int fw[4] = {nr.x, nr.y, nr.z, nr.w};
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             // (the face type comes from the references, already in registers,
             // so the neighbour loads need not wait for the record)
-            if (nr[a * 3] < 0) continue;
+            const int wd = fw[a];
+            if (wd < 0) continue;
             const T ca = rec[17 + a];
+            const T* src = ((wd & 1) ? prev : cur) + pop + (size_t)(wd >> 7) * 4;
             // the neighbour's values at this cell's face vertices (j != a, ascending)
             T g[4] = {T(0), T(0), T(0), T(0)};
             T gs = T(0);
@@ -220,8 +225,7 @@ __global__ void __launch_bounds__(kTetSweepThreads, 2) tet_sweep_kernel(TetArgs 
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (j == a) continue;
-                const int ref = nr[a * 3 + jj];
-                g[j] = ((ref & 1) ? prev : cur)[pop + (ref >> 1)] - r;
+                g[j] = src[(wd >> (5 - 2 * jj)) & 3] - r;
                 gs += g[j];
                 ++jj;
             }
@@ -239,42 +243,30 @@ __global__ void __launch_bounds__(kTetSweepThreads, 2) tet_sweep_kernel(TetArgs 
         }
         store4(cur + pop + (size_t)c * 4, x);
     };
-    auto refs = [&](int pos, int (&nr)[12]) {
-        const int4* q = reinterpret_cast<const int4*>(fref + (size_t)pos * 12);
-#pragma unroll
-        for (int w = 0; w < 3; ++w) {
-            const int4 e = q[w];
-            nr[4 * w] = e.x;
-            nr[4 * w + 1] = e.y;
-            nr[4 * w + 2] = e.z;
-            nr[4 * w + 3] = e.w;
-        }
-    };
+    auto refs = [&](int pos) { return reinterpret_cast<const int4*>(fref)[pos]; };
 
     // this thread's first pair of the coming level: cell and face references
-    int cn = 0, nrn[12];
+    int cn = 0;
+    int4 nrn = make_int4(-1, -1, -1, -1);
     if (lb < le && tid < (A.bounds[lb + 1] - A.bounds[lb]) * m) {
         const int pos = A.bounds[lb] + tid / m;
         cn = order[pos];
-        refs(pos, nrn);
+        nrn = refs(pos);
     }
     for (int l = lb; l < le; ++l) {
         const int p0 = A.bounds[l], p1 = A.bounds[l + 1];
         const int items = (p1 - p0) * m;
-        int cc = cn, nrc[12];
-#pragma unroll
-        for (int i = 0; i < 12; ++i) nrc[i] = nrn[i];
+        const int cc = cn;
+        const int4 nrc = nrn;
         if (l + 1 < le && tid < (A.bounds[l + 2] - p1) * m) {
             const int pos = p1 + tid / m;
             cn = order[pos];
-            refs(pos, nrn);
+            nrn = refs(pos);
         }
         if (tid < items) solve(p0 + tid / m, tid % m, cc, nrc);
         for (int it = tid + nt; it < items; it += nt) {
             const int pos = p0 + it / m;
-            int nr[12];
-            refs(pos, nr);
-            solve(pos, it % m, order[pos], nr);
+            solve(pos, it % m, order[pos], refs(pos));
         }
         __syncthreads();     // the next level reads this level's cells
     }
