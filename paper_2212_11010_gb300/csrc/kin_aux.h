@@ -91,7 +91,7 @@ cudaError_t sx_launch_relax(const SxArgs& a, int prec, cudaStream_t st);
 cudaError_t sx_launch_init(const SxArgs& a, const double* W, int prec, cudaStream_t st);
 
 // ---- tetrahedral meshes (kin_tet.cu) ----
-constexpr int kTetRec = 24;       // coefficient slots per (velocity, cell)
+constexpr int kTetRec = 21;       // coefficient slots per (velocity, cell): A^{-1}, |L|/20, four face factors
 constexpr int kTetSweepThreads = 640;
 
 struct TetSetupArgs {

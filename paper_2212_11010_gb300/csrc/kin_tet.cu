@@ -124,7 +124,6 @@ __global__ void tet_setup_kernel(TetSetupArgs A)
         for (int j = 0; j < 4; ++j) rec[i * 4 + j] = M[i][4 + j];
     rec[16] = vol / 20.0;
     for (int a = 0; a < 4; ++a) rec[17 + a] = cin[a];
-    for (int q = 21; q < kTetRec; ++q) rec[q] = 0.0;
     if (A.c32) {
         float* r32 = A.c32 + ((size_t)k * A.ncells + pos) * kTetRec;
         for (int q = 0; q < kTetRec; ++q) r32[q] = (float)rec[q];
